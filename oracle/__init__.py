@@ -1,0 +1,252 @@
+"""FP64 CPU oracle of the FDK hot path (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the ``cpu_baseline`` / reference leg of ``bench.py``.  The library path
+(``paper_1909_02724_gb300``) never imports this package, and this package
+imports nothing from it: the two share no code.
+
+The arithmetic lives in ``ifdk_oracle.c`` (plain C, FP64, built with
+``-O2 -ffp-contract=off``, no fast-math); this module only builds it with gcc
+and marshals numpy arrays.  Each function names the passage of the paper it
+follows (Chen et al., SC'19, arXiv 1909.02724):
+
+* ``projection_matrices`` -- Eq. 2 with the M0 / Mrot / M1 matrices of Sec. 3.2.1
+* ``cosine_weight``, ``ramlak``, ``filter_rows`` -- Algorithm 1
+* ``backproject``, ``backproject_voxels`` -- Algorithm 2 with Algorithm 3
+* ``project`` -- the exact adjoint of ``backproject``
+
+Geometry is passed as any object with the attributes of
+``paper_1909_02724_gb300.geometry.Geometry`` (read by attribute name only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ifdk_oracle.c")
+_LIBDIR = os.path.join(_HERE, "lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ifdk_oracle.c into oracle/lib/liboracle.so with gcc."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c11", "-D_GNU_SOURCE", "-O2", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [
+        ("sid", ctypes.c_double), ("sdd", ctypes.c_double),
+        ("nu", ctypes.c_int), ("nv", ctypes.c_int),
+        ("du", ctypes.c_double), ("dv", ctypes.c_double),
+        ("off_u", ctypes.c_double), ("off_v", ctypes.c_double),
+        ("np", ctypes.c_int), ("angles", ctypes.POINTER(ctypes.c_double)),
+        ("view_weights", ctypes.POINTER(ctypes.c_double)),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("vol_off_z", ctypes.c_double),
+    ]
+
+
+_P = ctypes.POINTER
+_d = ctypes.c_double
+_i64 = ctypes.c_int64
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            G = _P(_Geom)
+            lib.orc_projection_matrix.argtypes = [G, ctypes.c_int, _P(_d)]
+            lib.orc_view_weight.argtypes = [G, ctypes.c_int]
+            lib.orc_view_weight.restype = _d
+            lib.orc_cosine_weight.argtypes = [G, _P(_d)]
+            lib.orc_ramlak.argtypes = [ctypes.c_int, _P(_d)]
+            for f in (lib.orc_filter_rows_direct, lib.orc_filter_rows_fft):
+                f.argtypes = [G, _P(_d), _P(ctypes.c_int), ctypes.c_int, _P(_d)]
+            lib.orc_backproject.argtypes = [G, _P(_d), ctypes.c_int, ctypes.c_int, _P(_d), ctypes.c_int]
+            lib.orc_backproject.restype = ctypes.c_int
+            lib.orc_backproject_voxels.argtypes = [G, _P(_d), _P(_i64), _P(_i64), _i64, _P(_d),
+                                                   ctypes.c_int]
+            lib.orc_backproject_voxels.restype = ctypes.c_int
+            lib.orc_rows_needed.argtypes = [G, _P(_i64), _i64, _P(ctypes.c_ubyte)]
+            lib.orc_project.argtypes = [G, _P(_d), ctypes.c_int, ctypes.c_int, _P(_d), ctypes.c_int]
+            lib.orc_project.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray, ct=_d):
+    return a.ctypes.data_as(_P(ct))
+
+
+class _GeomHolder:
+    """Keeps the numpy arrays alive for as long as the ctypes struct is used."""
+
+    def __init__(self, geom):
+        self.angles = np.ascontiguousarray(np.asarray(geom.angles, dtype=np.float64))
+        w = getattr(geom, "view_weights", None)
+        self.weights = None if w is None else np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+        self.s = _Geom(
+            float(geom.sid), float(geom.sdd), int(geom.nu), int(geom.nv), float(geom.du),
+            float(geom.dv), float(geom.off_u), float(geom.off_v), int(len(self.angles)),
+            _ptr(self.angles), None if self.weights is None else _ptr(self.weights),
+            int(geom.nx), int(geom.ny), int(geom.nz), float(geom.dx), float(geom.dy),
+            float(geom.dz), float(geom.vol_off_z))
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def projection_matrices(geom) -> np.ndarray:
+    """P_s (np x 3 x 4), Eq. 2: first three rows of M1 . Mrot(beta_s) . M0."""
+    lib, g = _load(), _GeomHolder(geom)
+    out = np.empty((len(g.angles), 3, 4))
+    for s in range(len(g.angles)):
+        lib.orc_projection_matrix(g.ref, s, _ptr(out[s]))
+    return out
+
+
+def view_weights(geom) -> np.ndarray:
+    """Angular weight dbeta_s of each view (the spacing rule, or the user's weights)."""
+    lib, g = _load(), _GeomHolder(geom)
+    return np.array([lib.orc_view_weight(g.ref, s) for s in range(len(g.angles))])
+
+
+def cosine_weight(geom) -> np.ndarray:
+    """F_cos (nv x nu), Table 1 / Algorithm 1: D / sqrt(D^2 + a^2 + b^2)."""
+    lib, g = _load(), _GeomHolder(geom)
+    out = np.empty((geom.nv, geom.nu))
+    lib.orc_cosine_weight(g.ref, _ptr(out))
+    return out
+
+
+def ramlak(n: int) -> np.ndarray:
+    """Ram-Lak taps h(m), m = -(n-1)..n-1 (index m + n - 1)."""
+    out = np.empty(2 * n - 1)
+    _load().orc_ramlak(int(n), _ptr(out))
+    return out
+
+
+def filter_rows(geom, E_rows: np.ndarray, rows_v: np.ndarray, method: str = "auto") -> np.ndarray:
+    """Algorithm 1 on selected rows: Q = F_ramp (x) (E . F_cos).
+
+    E_rows: (R, nu) raw projection rows; rows_v: (R,) detector row index of each
+    (selects the F_cos row).  method: 'direct', 'fft' or 'auto' (fft for nu >= 256).
+    """
+    lib, g = _load(), _GeomHolder(geom)
+    E_rows = np.ascontiguousarray(E_rows, dtype=np.float64).reshape(-1, geom.nu)
+    rows_v = np.ascontiguousarray(rows_v, dtype=np.int32).reshape(-1)
+    assert rows_v.shape[0] == E_rows.shape[0]
+    Q = np.empty_like(E_rows)
+    if method == "auto":
+        method = "fft" if geom.nu >= 256 else "direct"
+    fn = lib.orc_filter_rows_fft if method == "fft" else lib.orc_filter_rows_direct
+    n = E_rows.shape[0]
+    nth = min(default_threads(), max(1, n // 64))
+    if nth <= 1:
+        fn(g.ref, _ptr(E_rows), _ptr(rows_v, ctypes.c_int), n, _ptr(Q))
+        return Q
+    bounds = np.linspace(0, n, nth + 1).astype(int)
+
+    def work(a, b):
+        fn(g.ref, _ptr(E_rows[a:b]), _ptr(rows_v[a:b], ctypes.c_int), b - a, _ptr(Q[a:b]))
+
+    ts = [threading.Thread(target=work, args=(int(a), int(b))) for a, b in zip(bounds[:-1], bounds[1:])]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return Q
+
+
+def filter_views(geom, E: np.ndarray, method: str = "auto") -> np.ndarray:
+    """Algorithm 1 on whole views: E (np, nv, nu) -> Q (np, nv, nu)."""
+    npv = E.shape[0]
+    rows_v = np.tile(np.arange(geom.nv, dtype=np.int32), npv)
+    return filter_rows(geom, E.reshape(-1, geom.nu), rows_v, method).reshape(E.shape)
+
+
+def backproject(geom, Q: np.ndarray, view_begin: int = 0, view_count: int | None = None,
+                vol: np.ndarray | None = None, threads: int | None = None) -> np.ndarray:
+    """Algorithm 2 (+ Algorithm 3, FDK weight): vol[i][j][k] += sum_s w_s f^2 interp2(Q_s, u, v)."""
+    lib, g = _load(), _GeomHolder(geom)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    assert Q.shape == (len(g.angles), geom.nv, geom.nu)
+    if view_count is None:
+        view_count = len(g.angles) - view_begin
+    if vol is None:
+        vol = np.zeros((geom.nx, geom.ny, geom.nz))
+    assert vol.dtype == np.float64 and vol.flags.c_contiguous
+    rc = lib.orc_backproject(g.ref, _ptr(Q), int(view_begin), int(view_count), _ptr(vol),
+                             int(threads or default_threads()))
+    assert rc == 0
+    return vol
+
+
+def backproject_voxels(geom, Q: np.ndarray, voxels: np.ndarray, rowmap: np.ndarray | None = None,
+                       threads: int | None = None) -> np.ndarray:
+    """Algorithm 2 at selected voxels (N x 3 int array of (i, j, k)), all views.
+
+    Q: dense (np, nv, nu), or sparse rows (R, nu) addressed by rowmap (np, nv) (-1 = absent).
+    """
+    lib, g = _load(), _GeomHolder(geom)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    vox = np.ascontiguousarray(voxels, dtype=np.int64).reshape(-1, 3)
+    out = np.empty(vox.shape[0])
+    rm = None if rowmap is None else np.ascontiguousarray(rowmap, dtype=np.int64)
+    rc = lib.orc_backproject_voxels(g.ref, _ptr(Q), None if rm is None else _ptr(rm, _i64),
+                                    _ptr(vox, _i64), vox.shape[0], _ptr(out),
+                                    int(threads or default_threads()))
+    if rc != 0:
+        raise RuntimeError("backproject_voxels: a needed detector row was not supplied")
+    return out
+
+
+def rows_needed(geom, voxels: np.ndarray) -> np.ndarray:
+    """Boolean (np, nv) mask of the detector rows that the voxels' bilinear taps touch."""
+    lib, g = _load(), _GeomHolder(geom)
+    vox = np.ascontiguousarray(voxels, dtype=np.int64).reshape(-1, 3)
+    need = np.zeros((len(g.angles), geom.nv), dtype=np.uint8)
+    lib.orc_rows_needed(g.ref, _ptr(vox, _i64), vox.shape[0], _ptr(need, ctypes.c_ubyte))
+    return need.astype(bool)
+
+
+def project(geom, vol: np.ndarray, view_begin: int = 0, view_count: int | None = None,
+            out: np.ndarray | None = None, threads: int | None = None) -> np.ndarray:
+    """Exact adjoint of ``backproject``: weighted bilinear splat of the volume into the views."""
+    lib, g = _load(), _GeomHolder(geom)
+    vol = np.ascontiguousarray(vol, dtype=np.float64)
+    assert vol.shape == (geom.nx, geom.ny, geom.nz)
+    if view_count is None:
+        view_count = len(g.angles) - view_begin
+    if out is None:
+        out = np.zeros((len(g.angles), geom.nv, geom.nu))
+    lib.orc_project(g.ref, _ptr(vol), int(view_begin), int(view_count), _ptr(out),
+                    int(threads or default_threads()))
+    return out
+
+
+def fdk(geom, E: np.ndarray, threads: int | None = None) -> np.ndarray:
+    """Full FDK in FP64: Algorithm 1 then Algorithm 2."""
+    return backproject(geom, filter_views(geom, np.asarray(E, dtype=np.float64)), threads=threads)
