@@ -1,0 +1,167 @@
+/*
+ * ifdk.h -- C-ABI of the GB300-native FDK hot path of iFDK
+ * (Chen, Wahib, Takizawa, Takano, Matsuoka, SC'19, arXiv 1909.02724).
+ *
+ * The library reconstructs a volume from circular cone-beam projections with
+ * the FDK method: a filtering stage (cosine weight, then a Ram-Lak ramp
+ * convolution along each detector row; Algorithm 1) and a voxel-driven
+ * back-projection using the reduced-cost coordinate scheme of Algorithm 4
+ * (Theorems 1-3).  It also provides the exact adjoint of the back-projection.
+ *
+ * Conventions shared by every call
+ *   - Problem Nu x Nv x Np -> Nx x Ny x Nz (Sec. 2.3, definition I).
+ *   - Projections E, Q, P: row-major [np][nv][nu] (U fastest), device memory.
+ *   - Volume: row-major [nx][ny][nz] (k fastest: the k-major layout of
+ *     Algorithm 4), device memory, FP32.
+ *   - Voxel (i,j,k) sits at world X = dx (i-(nx-1)/2), Y = -dy (j-(ny-1)/2),
+ *     Z = -dz (k-(nz-1)/2) + vol_off_z (the index flips of M0 in Eq. 2).
+ *   - View s rotates the object by +angles[s] about Z (Mrot); the source sits
+ *     at (-d sin b, -d cos b, 0); pixel (iu, iv) is centred at index position,
+ *     principal point ((nu-1)/2 + off_u/du, (nv-1)/2 + off_v/dv) (M1).
+ *   - Ownership: the caller owns every data buffer and stream; a plan owns only
+ *     its immutable geometry tables (and a device status word).
+ *   - Asynchrony: filter / backproject / project enqueue kernels on `stream`
+ *     (a cudaStream_t; NULL = the legacy default stream), allocate nothing,
+ *     and do not synchronise.  Outputs of backproject / project ACCUMULATE:
+ *     the caller zeroes them first.  This is what makes view chunking,
+ *     checkpoint/resume (volume + next view index) and adjoint sums exact.
+ *   - Errors: every call returns an ifdk_status (0 = success, negative =
+ *     failure); argument errors are detected before any launch and leave all
+ *     buffers untouched.  Nothing is thrown or printed.  Faults found on the
+ *     device (a bounded wait that ran out) are latched in the plan's status
+ *     word and reported by ifdk_last_device_status.
+ *   - One plan is used by one host thread at a time; calls on one plan may be
+ *     enqueued on any streams (the kernels only read the plan's tables).
+ */
+#ifndef IFDK_H
+#define IFDK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ifdk_plan_s *ifdk_plan;
+
+/* Circular cone-beam geometry (Table 1).  Lengths in mm, angles in rad.
+   `angles` (and `view_weights` if not NULL) are host arrays of np doubles,
+   copied by ifdk_create. */
+typedef struct {
+    double sid, sdd;            /* d: source to rotation axis, D: source to detector */
+    int nu, nv;                 /* detector width (U) and height (V), pixels */
+    double du, dv;              /* detector pitch, mm/pixel */
+    double off_u, off_v;        /* principal point offset from the detector centre, mm */
+    int np;                     /* number of views */
+    const double *angles;       /* np view angles (rad) */
+    const double *view_weights; /* np angular weights (rad), or NULL: half the angular
+                                   distance to the two neighbouring views (2 pi / np
+                                   for a uniform full scan) */
+    int nx, ny, nz;             /* volume size, voxels */
+    double dx, dy, dz;          /* voxel pitch, mm/voxel */
+    double vol_off_z;           /* world Z of the volume centre, mm */
+} ifdk_geometry;
+
+/* Storage types of filtered projections. */
+enum { IFDK_F32 = 0, IFDK_F16 = 1, IFDK_BF16 = 2 };
+
+/* Status codes. */
+enum {
+    IFDK_OK = 0,
+    IFDK_ERR_INVALID = -1,      /* NULL pointer, bad size, range or enum */
+    IFDK_ERR_GEOMETRY = -2,     /* geometry the method does not cover (e.g. a voxel
+                                   behind the source plane, non-positive pitch) */
+    IFDK_ERR_ALIGNMENT = -3,    /* a buffer is not 16-byte aligned */
+    IFDK_ERR_CUDA = -4,         /* a CUDA runtime call failed (no device, launch error) */
+    IFDK_ERR_TIMEOUT = -5,      /* a bounded device wait ran out (device status) */
+    IFDK_ERR_NOMEM = -6,        /* ifdk_create could not allocate its tables */
+    IFDK_ERR_UNSUPPORTED = -7   /* valid request the library does not implement */
+};
+
+/* Builds a plan: FP64 per-view projection terms P_s = (M1 . Mrot(b_s) . M0)[0:3]
+   (Eq. 2) re-centred on the volume and principal point, the FDK view weights
+   dbeta_s * d * D / (2 du), the cosine table F_cos (Table 1, Algorithm 1) and
+   the Ram-Lak taps h(0)=1/4, h(odd n)=-1/(pi^2 n^2) (Kak & Slaney); everything
+   is cast to FP32 and uploaded to the current CUDA device.  Validates the
+   geometry (positive sizes and pitches, every voxel in front of the source).
+   *out receives the plan, or NULL on failure.  Synchronous. */
+int ifdk_create(ifdk_plan *out, const ifdk_geometry *g);
+
+/* Releases a plan (device tables included).  NULL is accepted.  The caller
+   makes sure no work using the plan is still in flight. */
+int ifdk_destroy(ifdk_plan p);
+
+/* Filtering stage, Algorithm 1: Q[s][v][n] = sum_m h(n-m) F_cos[v][m] E[s][v][m]
+   for the np views: the cosine weight followed by an exact linear (zero-padded)
+   Ram-Lak convolution of every detector row.
+   E: device FP32 [np][nv][nu], read only.  Q: device [np][nv][nu] of q_dtype
+   (IFDK_F32, IFDK_F16 or IFDK_BF16), overwritten.  split_terms selects the
+   operand precision of the tensor-core Toeplitz product (1..3 BF16 terms per
+   operand); 0 selects the FP32 SIMT kernel.  E and Q must not overlap. */
+int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms,
+                void *stream);
+
+/* Adjoint of ifdk_filter for FP32 (the Toeplitz matrix is symmetric because h
+   is even, and F_cos is diagonal): G_E[s][v][m] = F_cos[v][m] sum_n h(n-m) G_Q[s][v][n].
+   G_Q, G_E: device FP32 [np][nv][nu]; G_E is overwritten. */
+int ifdk_filter_adjoint(ifdk_plan p, const float *G_Q, float *G_E, void *stream);
+
+/* Back-projection, Algorithm 4: for every voxel and view s in
+   [view_begin, view_begin+view_count):
+     vol[i][j][k] += w_s f^2 interp2(Q_s, u, v),  f = 1/z,
+   with (x, y, z) = P_s (i, j, k, 1), u = x f, v = y f (Eq. 2); interp2 is the
+   bilinear interpolation of Algorithm 3 with floor and zero outside the
+   detector; w_s = dbeta_s d D / (2 du) is the FDK constant.  Voxel pairs
+   (k, nz-1-k) share u, f and W (Theorems 1-3) when the volume is centred.
+   Q: device [np][nv][nu] of q_dtype (the full view set; only the requested
+   range is read), 16-byte aligned.  vol: device FP32, 16-byte aligned,
+   ACCUMULATED into.  Q and vol must not overlap. */
+int ifdk_backproject(ifdk_plan p, const void *Q, int q_dtype, int view_begin, int view_count,
+                     float *vol, void *stream);
+
+/* Exact adjoint of ifdk_backproject (FP32): for every voxel, view in the
+   range and bilinear tap, P[s][tap] += w_s f^2 (bilinear weight) vol[i][j][k].
+   It is the transpose of the back-projection matrix, not a physical line-
+   integral projector.  vol: device FP32 [nx][ny][nz]; P: device FP32
+   [np][nv][nu], ACCUMULATED into (floating-point atomics: the summation order,
+   hence the last bits, may differ between runs). */
+int ifdk_project(ifdk_plan p, const float *vol, float *P, int view_begin, int view_count,
+                 void *stream);
+
+/* Reads and clears the plan's device status word on `stream` (synchronises
+   that stream).  Returns IFDK_OK, IFDK_ERR_TIMEOUT if a bounded wait inside a
+   kernel ran out since the last call, or IFDK_ERR_CUDA. */
+int ifdk_last_device_status(ifdk_plan p, void *stream);
+
+/* Sets the limit of every bounded device wait launched with this plan, in
+   nanoseconds (default 2e9).  0 restores the default. */
+int ifdk_set_wait_limit(ifdk_plan p, uint64_t nanoseconds);
+
+/* Self-test of the bounded-wait machinery: launches one block that waits on an
+   mbarrier nothing arrives at, for at most `nanoseconds`, then records
+   IFDK_ERR_TIMEOUT in the status word and exits cleanly.  Asynchronous. */
+int ifdk_wait_selftest(ifdk_plan p, uint64_t nanoseconds, void *stream);
+
+/* Describes the launch the plan chose for ifdk_backproject with q_dtype:
+   info[0] = path (1 = mirror-pair fold kernel, 0 = general kernel),
+   info[1] = TMA box width (pixels), info[2] = box height (rows),
+   info[3] = z pairs per thread, info[4] = views per shared-memory chunk,
+   info[5] = dynamic shared memory bytes per block, info[6] = blocks in the grid
+   (per launch of at most info[7] views), info[7] = views per launch. */
+int ifdk_backproject_info(ifdk_plan p, int q_dtype, int64_t info[8]);
+
+/* Host-only query (no device needed): the launch ifdk_backproject would use
+   for this geometry and q_dtype, in the layout of ifdk_backproject_info,
+   plus info[8] = fold width (elements) and info[9] = u alignment of the box
+   start (elements).  Returns the geometry's validation status. */
+int ifdk_query_backproject(const ifdk_geometry *g, int q_dtype, int64_t info[10]);
+
+/* Human-readable text for a status code (static storage). */
+const char *ifdk_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IFDK_H */

@@ -1,0 +1,273 @@
+"""ctypes binding of the ifdk C-ABI (``include/ifdk.h``).
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+library.  The functions keep the C names (``ifdk_create``, ``ifdk_filter``,
+``ifdk_backproject``, ``ifdk_project`` ...); they accept torch CUDA tensors
+(or raw device addresses) and enqueue on the current torch stream unless a
+stream is given.  If the library is not built this module raises on first use:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .geometry import Geometry
+
+_LIBDIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib")
+LIB_PATH = os.path.join(_LIBDIR, "libifdk.so")
+
+IFDK_F32, IFDK_F16, IFDK_BF16 = 0, 1, 2
+IFDK_OK = 0
+IFDK_ERR_INVALID, IFDK_ERR_GEOMETRY, IFDK_ERR_ALIGNMENT, IFDK_ERR_CUDA = -1, -2, -3, -4
+IFDK_ERR_TIMEOUT, IFDK_ERR_NOMEM, IFDK_ERR_UNSUPPORTED = -5, -6, -7
+
+# every symbol include/ifdk.h declares
+EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_adjoint", "ifdk_backproject",
+           "ifdk_project", "ifdk_last_device_status", "ifdk_set_wait_limit", "ifdk_wait_selftest",
+           "ifdk_backproject_info", "ifdk_query_backproject", "ifdk_status_string")
+
+
+class IfdkError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+
+
+class _GeometryC(ctypes.Structure):
+    _fields_ = [
+        ("sid", ctypes.c_double), ("sdd", ctypes.c_double),
+        ("nu", ctypes.c_int), ("nv", ctypes.c_int),
+        ("du", ctypes.c_double), ("dv", ctypes.c_double),
+        ("off_u", ctypes.c_double), ("off_v", ctypes.c_double),
+        ("np", ctypes.c_int), ("angles", ctypes.POINTER(ctypes.c_double)),
+        ("view_weights", ctypes.POINTER(ctypes.c_double)),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("vol_off_z", ctypes.c_double),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libifdk.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"ifdk CUDA library not built ({path}); run "
+                               "paper_1909_02724_gb300.build.build() -- there is no CPU fallback")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        lib.ifdk_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_GeometryC)]
+        lib.ifdk_destroy.argtypes = [vp]
+        lib.ifdk_filter.argtypes = [vp, vp, vp, i32, i32, vp]
+        lib.ifdk_filter_adjoint.argtypes = [vp, vp, vp, vp]
+        lib.ifdk_backproject.argtypes = [vp, vp, i32, i32, i32, vp, vp]
+        lib.ifdk_project.argtypes = [vp, vp, vp, i32, i32, vp]
+        lib.ifdk_last_device_status.argtypes = [vp, vp]
+        lib.ifdk_set_wait_limit.argtypes = [vp, ctypes.c_uint64]
+        lib.ifdk_wait_selftest.argtypes = [vp, ctypes.c_uint64, vp]
+        lib.ifdk_backproject_info.argtypes = [vp, i32, ctypes.POINTER(i64)]
+        lib.ifdk_query_backproject.argtypes = [ctypes.POINTER(_GeometryC), i32, ctypes.POINTER(i64)]
+        lib.ifdk_status_string.argtypes = [i32]
+        lib.ifdk_status_string.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name != "ifdk_status_string":
+                getattr(lib, name).restype = i32
+        _lib = lib
+        return lib
+
+
+def status_string(code: int) -> str:
+    return load_library().ifdk_status_string(int(code)).decode()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != IFDK_OK:
+        raise IfdkError(rc, what)
+
+
+def _addr(x) -> int | None:
+    """Device address of a torch tensor (or an int address / None)."""
+    if x is None or isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def dtype_code(t) -> int:
+    import torch
+    m = {torch.float32: IFDK_F32, torch.float16: IFDK_F16, torch.bfloat16: IFDK_BF16}
+    if t not in m:
+        raise TypeError(f"unsupported projection storage type {t}")
+    return m[t]
+
+
+class _GeomHolder:
+    def __init__(self, g: Geometry):
+        import numpy as np
+        self.angles = np.ascontiguousarray(g.angles, dtype=np.float64)
+        self.weights = None if g.view_weights is None else np.ascontiguousarray(g.view_weights, dtype=np.float64)
+        P = ctypes.POINTER(ctypes.c_double)
+        self.c = _GeometryC(
+            float(g.sid), float(g.sdd), int(g.nu), int(g.nv), float(g.du), float(g.dv),
+            float(g.off_u), float(g.off_v), int(self.angles.shape[0]), self.angles.ctypes.data_as(P),
+            None if self.weights is None else self.weights.ctypes.data_as(P),
+            int(g.nx), int(g.ny), int(g.nz), float(g.dx), float(g.dy), float(g.dz), float(g.vol_off_z))
+
+
+def ifdk_create(geom: Geometry) -> int:
+    lib = load_library()
+    h = _GeomHolder(geom)
+    out = ctypes.c_void_p()
+    _check(lib.ifdk_create(ctypes.byref(out), ctypes.byref(h.c)), "ifdk_create")
+    return int(out.value)
+
+
+def ifdk_destroy(plan: int) -> None:
+    _check(load_library().ifdk_destroy(plan), "ifdk_destroy")
+
+
+def ifdk_filter(plan: int, E, Q, q_dtype: int, split_terms: int = 0, stream=None) -> None:
+    _check(load_library().ifdk_filter(plan, _addr(E), _addr(Q), int(q_dtype), int(split_terms),
+                                      _stream(stream)), "ifdk_filter")
+
+
+def ifdk_filter_adjoint(plan: int, G_Q, G_E, stream=None) -> None:
+    _check(load_library().ifdk_filter_adjoint(plan, _addr(G_Q), _addr(G_E), _stream(stream)),
+           "ifdk_filter_adjoint")
+
+
+def ifdk_backproject(plan: int, Q, q_dtype: int, view_begin: int, view_count: int, vol, stream=None) -> None:
+    _check(load_library().ifdk_backproject(plan, _addr(Q), int(q_dtype), int(view_begin), int(view_count),
+                                           _addr(vol), _stream(stream)), "ifdk_backproject")
+
+
+def ifdk_project(plan: int, vol, P, view_begin: int, view_count: int, stream=None) -> None:
+    _check(load_library().ifdk_project(plan, _addr(vol), _addr(P), int(view_begin), int(view_count),
+                                       _stream(stream)), "ifdk_project")
+
+
+def ifdk_last_device_status(plan: int, stream=None) -> int:
+    return int(load_library().ifdk_last_device_status(plan, _stream(stream)))
+
+
+def ifdk_set_wait_limit(plan: int, nanoseconds: int) -> None:
+    _check(load_library().ifdk_set_wait_limit(plan, int(nanoseconds)), "ifdk_set_wait_limit")
+
+
+def ifdk_wait_selftest(plan: int, nanoseconds: int, stream=None) -> None:
+    _check(load_library().ifdk_wait_selftest(plan, int(nanoseconds), _stream(stream)), "ifdk_wait_selftest")
+
+
+def ifdk_backproject_info(plan: int, q_dtype: int) -> dict:
+    arr = (ctypes.c_int64 * 8)()
+    _check(load_library().ifdk_backproject_info(plan, int(q_dtype), arr), "ifdk_backproject_info")
+    keys = ("path", "box_w", "box_h", "z_per_thread", "views_per_chunk", "smem_bytes", "blocks",
+            "views_per_launch")
+    return dict(zip(keys, (int(v) for v in arr)))
+
+
+def ifdk_query_backproject(geom: Geometry, q_dtype: int) -> dict:
+    """Host-only: the launch ifdk_backproject would choose (no device needed)."""
+    h = _GeomHolder(geom)
+    arr = (ctypes.c_int64 * 10)()
+    _check(load_library().ifdk_query_backproject(ctypes.byref(h.c), int(q_dtype), arr),
+           "ifdk_query_backproject")
+    keys = ("path", "box_w", "box_h", "z_per_thread", "views_per_chunk", "smem_bytes", "blocks",
+            "views_per_launch", "fold_w", "align")
+    return dict(zip(keys, (int(v) for v in arr)))
+
+
+class Plan:
+    """Owns an ifdk plan for one geometry; methods take torch CUDA tensors."""
+
+    def __init__(self, geom: Geometry):
+        self.geom = geom
+        self.handle = ifdk_create(geom)
+
+    def close(self) -> None:
+        if self.handle:
+            ifdk_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_views(self, t, name):
+        g = self.geom
+        if not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != (g.np, g.nv, g.nu):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of shape {(g.np, g.nv, g.nu)}")
+
+    def _check_vol(self, t):
+        import torch
+        g = self.geom
+        if (not t.is_cuda or not t.is_contiguous() or t.dtype != torch.float32
+                or tuple(t.shape) != (g.nx, g.ny, g.nz)):
+            raise ValueError(f"vol must be a contiguous float32 CUDA tensor of shape {(g.nx, g.ny, g.nz)}")
+
+    def filter(self, E, Q=None, dtype=None, split_terms: int = 0, stream=None):
+        import torch
+        self._check_views(E, "E")
+        if E.dtype != torch.float32:
+            raise ValueError("E must be float32")
+        if Q is None:
+            Q = torch.empty_like(E, dtype=dtype or torch.float32)
+        self._check_views(Q, "Q")
+        ifdk_filter(self.handle, E, Q, dtype_code(Q.dtype), split_terms, stream)
+        return Q
+
+    def filter_adjoint(self, G_Q, out=None, stream=None):
+        import torch
+        self._check_views(G_Q, "G_Q")
+        if out is None:
+            out = torch.empty_like(G_Q)
+        ifdk_filter_adjoint(self.handle, G_Q, out, stream)
+        return out
+
+    def backproject(self, Q, vol=None, view_begin: int = 0, view_count: int | None = None, stream=None):
+        import torch
+        self._check_views(Q, "Q")
+        g = self.geom
+        if vol is None:
+            vol = torch.zeros((g.nx, g.ny, g.nz), dtype=torch.float32, device=Q.device)
+        self._check_vol(vol)
+        n = g.np - view_begin if view_count is None else view_count
+        ifdk_backproject(self.handle, Q, dtype_code(Q.dtype), view_begin, n, vol, stream)
+        return vol
+
+    def project(self, vol, P=None, view_begin: int = 0, view_count: int | None = None, stream=None):
+        import torch
+        self._check_vol(vol)
+        g = self.geom
+        if P is None:
+            P = torch.zeros((g.np, g.nv, g.nu), dtype=torch.float32, device=vol.device)
+        self._check_views(P, "P")
+        n = g.np - view_begin if view_count is None else view_count
+        ifdk_project(self.handle, vol, P, view_begin, n, stream)
+        return P
+
+    def device_status(self, stream=None) -> int:
+        return ifdk_last_device_status(self.handle, stream)
+
+    def info(self, dtype) -> dict:
+        import torch
+        code = dtype if isinstance(dtype, int) else dtype_code(dtype if dtype is not None else torch.float32)
+        return ifdk_backproject_info(self.handle, code)

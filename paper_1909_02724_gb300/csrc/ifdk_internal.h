@@ -1,0 +1,84 @@
+// Internal declarations of the ifdk library (not part of the C-ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "ifdk.h"
+
+namespace ifdk {
+
+// Per-view FP32 projection terms.  P_s (Eq. 2) is formed in FP64 on the host
+// and re-centred on the volume centre (i' = i - (nx-1)/2, ...) and on the
+// principal point, so that for voxel (i', j', k'):
+//   z = C0 i' + C1 j' + C3            (Theorem 3: no k' term)
+//   u = uc + (A0 i' + A1 j' + A3) / z (Theorem 2: no k' term)
+//   v = vc + (B2 k' + B3) / z         (no i', j' term in this geometry)
+// w is the FDK constant dbeta_s d D / (2 du) of the view.
+struct ViewTerms {
+    float A0, A1, A3, B2;
+    float B3, C0, C1, C3;
+    float w, pad0, pad1, pad2;
+};
+
+// Fold (mirror-pair) back-projection: block tile and staging constants.
+constexpr int kTileX = 16, kTileY = 16, kThreads = kTileX * kTileY;
+constexpr int kPairs = 16;       // z pairs per thread (the thread's z-run)
+constexpr int kViews = 4;        // max views per shared-memory chunk
+constexpr int kFoldPitchS = 33;  // fold row pitch (elements, odd: spreads banks) for widths <= 32
+constexpr int kFoldPitchL = 49;  // ... and for widths <= 48
+constexpr int kMargin = 1;       // window margin (pixels) on every side
+constexpr int kGenZ = 16;        // z voxels per thread in the general kernel
+
+struct BpLaunch {
+    int path;          // 1 = fold (mirror pairs, TMA), 0 = general
+    int fold_w;        // fold width (elements)
+    int box_w, box_h;  // TMA box (elements, rows)
+    int align;         // u alignment of the TMA box start (elements)
+    int pitch;         // fold row pitch (elements)
+    int views;         // views per shared-memory chunk
+    size_t smem;       // dynamic shared memory bytes
+    int grid_x, grid_y;
+};
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled();  // cuTensorMapEncodeTiled through the runtime's driver entry point
+
+inline size_t dtype_size(int t) { return t == IFDK_F32 ? 4 : 2; }
+
+}  // namespace ifdk
+
+struct ifdk_plan_s {
+    ifdk_geometry g;                  // copy; angles/view_weights point into the vectors below
+    std::vector<double> angles, weights;
+    std::vector<ifdk::ViewTerms> terms;  // host copy of the FP32 table
+    int device = 0;
+    ifdk::ViewTerms *d_terms = nullptr;  // [np]
+    float *d_fcos = nullptr;             // [nv][nu]
+    float *d_taps = nullptr;             // [2 nu - 1], index m + nu - 1
+    unsigned int *d_status = nullptr;    // device status word
+    double uc = 0, vc = 0;               // principal point (pixels)
+    int two_vc = 0;                      // 2 vc when it is an integer
+    bool fold_ok = false;                // mirror-pair fold path applicable
+    ifdk::BpLaunch bp[3];                // per storage type
+    unsigned long long wait_ns = 2000000000ull;
+};
+
+// Implemented in ifdk_bp.cu / ifdk_filter.cu / ifdk_project.cu.
+namespace ifdk {
+void plan_backproject(ifdk_plan_s *p);
+int launch_backproject(ifdk_plan_s *p, const void *Q, int q_dtype, int view_begin, int view_count,
+                       float *vol, cudaStream_t stream);
+int launch_filter(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int split_terms, bool adjoint,
+                  cudaStream_t stream);
+int launch_project(ifdk_plan_s *p, const float *vol, float *P, int view_begin, int view_count,
+                   cudaStream_t stream);
+int launch_wait_selftest(ifdk_plan_s *p, unsigned long long ns, cudaStream_t stream);
+}  // namespace ifdk

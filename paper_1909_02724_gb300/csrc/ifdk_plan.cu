@@ -1,0 +1,288 @@
+// Plan creation, validation, status handling and the C-ABI entry points.
+//
+// The plan forms every geometric quantity in FP64 (Eq. 2 projection terms,
+// FDK view weights, the F_cos table and the Ram-Lak taps of Algorithm 1) and
+// casts the results to FP32 device tables: these are the only FP64 steps.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "ifdk_device.cuh"
+#include "ifdk_internal.h"
+
+namespace ifdk {
+
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    });
+    return fn;
+}
+
+namespace {
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// Angular weight of view s: the caller's weight, or half the angular distance
+// to the two neighbouring views (differences wrapped into (-pi, pi]).
+double view_weight(const ifdk_plan_s &p, int s)
+{
+    const int n = p.g.np;
+    if (!p.weights.empty()) return p.weights[s];
+    if (n == 1) return 2.0 * M_PI;
+    const double *a = p.angles.data();
+    const double dp = std::remainder(a[(s + 1) % n] - a[s], 2.0 * M_PI);
+    const double dm = std::remainder(a[s] - a[(s + n - 1) % n], 2.0 * M_PI);
+    return 0.5 * (std::fabs(dp) + std::fabs(dm));
+}
+
+int validate(const ifdk_geometry *g)
+{
+    if (!g || g->np < 1 || g->nu < 2 || g->nv < 2 || g->nx < 1 || g->ny < 1 || g->nz < 1 || !g->angles)
+        return IFDK_ERR_INVALID;
+    if ((int64_t)g->nu * g->nv > (int64_t)1 << 30 || g->nx > 65536 || g->ny > 65536 || g->nz > 65536)
+        return IFDK_ERR_INVALID;
+    if (!finite_pos(g->sid) || !finite_pos(g->sdd) || !finite_pos(g->du) || !finite_pos(g->dv) ||
+        !finite_pos(g->dx) || !finite_pos(g->dy) || !finite_pos(g->dz))
+        return IFDK_ERR_GEOMETRY;
+    if (!std::isfinite(g->off_u) || !std::isfinite(g->off_v) || !std::isfinite(g->vol_off_z))
+        return IFDK_ERR_GEOMETRY;
+    if (g->sdd <= g->sid) return IFDK_ERR_GEOMETRY;
+    for (int s = 0; s < g->np; ++s) {
+        if (!std::isfinite(g->angles[s])) return IFDK_ERR_GEOMETRY;
+        if (g->view_weights && !std::isfinite(g->view_weights[s])) return IFDK_ERR_GEOMETRY;
+    }
+    // Every voxel must lie in front of the source plane with room to spare:
+    // z = d + Y' >= d - r_xy, r_xy the largest distance of a voxel from the axis.
+    const double hx = 0.5 * (g->nx - 1) * g->dx, hy = 0.5 * (g->ny - 1) * g->dy;
+    if (std::sqrt(hx * hx + hy * hy) >= 0.9 * g->sid) return IFDK_ERR_GEOMETRY;
+    return IFDK_OK;
+}
+
+// Host part of a plan: geometry copy, principal point, FP64 projection terms.
+int init_host_plan(ifdk_plan_s *p, const ifdk_geometry *gin)
+{
+    p->g = *gin;
+    p->angles.assign(gin->angles, gin->angles + gin->np);
+    if (gin->view_weights) p->weights.assign(gin->view_weights, gin->view_weights + gin->np);
+    p->g.angles = p->angles.data();
+    p->g.view_weights = p->weights.empty() ? nullptr : p->weights.data();
+    const ifdk_geometry &g = p->g;
+
+    p->uc = (g.nu - 1) / 2.0 + g.off_u / g.du;
+    p->vc = (g.nv - 1) / 2.0 + g.off_v / g.dv;
+    const double two_vc = 2.0 * p->vc;
+    p->two_vc = (int)std::lround(two_vc);
+    p->fold_ok = std::fabs(two_vc - p->two_vc) < 1e-9 && g.vol_off_z == 0.0;
+
+    // Per-view projection terms, FP64 (Eq. 2: M1 . Mrot(b) . M0, multiplied out
+    // in closed form and re-centred on the volume centre and principal point).
+    // World point of centred voxel (i', j', k'): X = dx i', Y = -dy j', Z = -dz k' + off_z.
+    // Mrot: X' = cos b X - sin b Y, Y' = sin b X + cos b Y; homogeneous z = d + Y'.
+    // M1:   u - uc = D X' / (du z),  v - vc = D (-Z) / (dv z).
+    p->terms.resize(g.np);
+    for (int s = 0; s < g.np; ++s) {
+        const double cb = std::cos(g.angles[s]), sb = std::sin(g.angles[s]);
+        ViewTerms &t = p->terms[s];
+        t.C0 = (float)(g.dx * sb);
+        t.C1 = (float)(-g.dy * cb);
+        t.C3 = (float)g.sid;
+        t.A0 = (float)(g.sdd * g.dx * cb / g.du);
+        t.A1 = (float)(g.sdd * g.dy * sb / g.du);
+        t.A3 = 0.0f;
+        t.B2 = (float)(g.sdd * g.dz / g.dv);
+        t.B3 = (float)(-g.sdd * g.vol_off_z / g.dv);
+        t.w = (float)(view_weight(*p, s) * g.sid * g.sdd / (2.0 * g.du));
+        t.pad0 = t.pad1 = t.pad2 = 0.0f;
+    }
+
+    return IFDK_OK;
+}
+
+}  // namespace
+}  // namespace ifdk
+
+using namespace ifdk;
+
+extern "C" {
+
+const char *ifdk_status_string(int code)
+{
+    switch (code) {
+    case IFDK_OK: return "ok";
+    case IFDK_ERR_INVALID: return "invalid argument";
+    case IFDK_ERR_GEOMETRY: return "geometry not covered";
+    case IFDK_ERR_ALIGNMENT: return "buffer not 16-byte aligned";
+    case IFDK_ERR_CUDA: return "CUDA runtime error";
+    case IFDK_ERR_TIMEOUT: return "bounded device wait ran out";
+    case IFDK_ERR_NOMEM: return "out of memory";
+    case IFDK_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+    }
+}
+
+int ifdk_create(ifdk_plan *out, const ifdk_geometry *gin)
+{
+    if (!out) return IFDK_ERR_INVALID;
+    *out = nullptr;
+    int rc = validate(gin);
+    if (rc != IFDK_OK) return rc;
+
+    ifdk_plan_s *p = new (std::nothrow) ifdk_plan_s();
+    if (!p) return IFDK_ERR_NOMEM;
+    rc = init_host_plan(p, gin);
+    if (rc != IFDK_OK) { delete p; return rc; }
+    const ifdk_geometry &g = p->g;
+
+    // Cosine weight D / sqrt(D^2 + a^2 + b^2) and Ram-Lak taps, FP64 then FP32.
+    std::vector<float> fcos((size_t)g.nu * g.nv), taps(2 * (size_t)g.nu - 1);
+    for (int iv = 0; iv < g.nv; ++iv)
+        for (int iu = 0; iu < g.nu; ++iu) {
+            const double a = (iu - p->uc) * g.du, b = (iv - p->vc) * g.dv;
+            fcos[(size_t)iv * g.nu + iu] = (float)(g.sdd / std::sqrt(g.sdd * g.sdd + a * a + b * b));
+        }
+    for (int m = -(g.nu - 1); m <= g.nu - 1; ++m) {
+        const double h = m == 0 ? 0.25 : (m % 2 == 0 ? 0.0 : -1.0 / (M_PI * M_PI * (double)m * m));
+        taps[m + g.nu - 1] = (float)h;
+    }
+
+    if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return IFDK_ERR_CUDA; }
+    bool ok = cudaMalloc(&p->d_terms, sizeof(ViewTerms) * g.np) == cudaSuccess &&
+              cudaMalloc(&p->d_fcos, sizeof(float) * fcos.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_taps, sizeof(float) * taps.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_status, sizeof(unsigned int)) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); ifdk_destroy(p); return IFDK_ERR_NOMEM; }
+    ok = cudaMemcpy(p->d_terms, p->terms.data(), sizeof(ViewTerms) * g.np, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(p->d_fcos, fcos.data(), sizeof(float) * fcos.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(p->d_taps, taps.data(), sizeof(float) * taps.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(p->d_status, 0, sizeof(unsigned int)) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); ifdk_destroy(p); return IFDK_ERR_CUDA; }
+
+    plan_backproject(p);
+    *out = p;
+    return IFDK_OK;
+}
+
+int ifdk_destroy(ifdk_plan p)
+{
+    if (!p) return IFDK_OK;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != p->device) cudaSetDevice(p->device);
+    cudaFree(p->d_terms);
+    cudaFree(p->d_fcos);
+    cudaFree(p->d_taps);
+    cudaFree(p->d_status);
+    if (dev >= 0 && dev != p->device) cudaSetDevice(dev);
+    delete p;
+    return IFDK_OK;
+}
+
+int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms, void *stream)
+{
+    if (!p || !E || !Q) return IFDK_ERR_INVALID;
+    if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
+    if (split_terms < 0 || split_terms > 3) return IFDK_ERR_INVALID;
+    return launch_filter(p, E, Q, q_dtype, split_terms, false, (cudaStream_t)stream);
+}
+
+int ifdk_filter_adjoint(ifdk_plan p, const float *G_Q, float *G_E, void *stream)
+{
+    if (!p || !G_Q || !G_E) return IFDK_ERR_INVALID;
+    return launch_filter(p, G_Q, G_E, IFDK_F32, 0, true, (cudaStream_t)stream);
+}
+
+int ifdk_backproject(ifdk_plan p, const void *Q, int q_dtype, int view_begin, int view_count,
+                     float *vol, void *stream)
+{
+    if (!p || !Q || !vol) return IFDK_ERR_INVALID;
+    if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
+    if (view_begin < 0 || view_count < 0 || view_begin > p->g.np || view_count > p->g.np - view_begin)
+        return IFDK_ERR_INVALID;
+    if (((uintptr_t)Q & 15) || ((uintptr_t)vol & 15)) return IFDK_ERR_ALIGNMENT;
+    if (view_count == 0) return IFDK_OK;
+    return launch_backproject(p, Q, q_dtype, view_begin, view_count, vol, (cudaStream_t)stream);
+}
+
+int ifdk_project(ifdk_plan p, const float *vol, float *P, int view_begin, int view_count, void *stream)
+{
+    if (!p || !vol || !P) return IFDK_ERR_INVALID;
+    if (view_begin < 0 || view_count < 0 || view_begin > p->g.np || view_count > p->g.np - view_begin)
+        return IFDK_ERR_INVALID;
+    if (((uintptr_t)vol & 15) || ((uintptr_t)P & 15)) return IFDK_ERR_ALIGNMENT;
+    if (view_count == 0) return IFDK_OK;
+    return launch_project(p, vol, P, view_begin, view_count, (cudaStream_t)stream);
+}
+
+int ifdk_last_device_status(ifdk_plan p, void *stream)
+{
+    if (!p) return IFDK_ERR_INVALID;
+    unsigned int h = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&h, p->d_status, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(p->d_status, 0, sizeof(unsigned int), s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return IFDK_ERR_CUDA;
+    if (h & kStatusTimeout) return IFDK_ERR_TIMEOUT;
+    return IFDK_OK;
+}
+
+int ifdk_set_wait_limit(ifdk_plan p, uint64_t ns)
+{
+    if (!p) return IFDK_ERR_INVALID;
+    p->wait_ns = ns ? ns : 2000000000ull;
+    return IFDK_OK;
+}
+
+int ifdk_wait_selftest(ifdk_plan p, uint64_t ns, void *stream)
+{
+    if (!p || ns == 0 || ns > 10000000000ull) return IFDK_ERR_INVALID;
+    return launch_wait_selftest(p, ns, (cudaStream_t)stream);
+}
+
+static void fill_info(const ifdk_plan_s *p, const BpLaunch &b, int64_t *info)
+{
+    info[0] = b.path;
+    info[1] = b.box_w;
+    info[2] = b.box_h;
+    info[3] = b.path ? kPairs : kGenZ;
+    info[4] = b.path ? b.views : 1;
+    info[5] = (int64_t)b.smem;
+    info[6] = (int64_t)b.grid_x * b.grid_y;
+    info[7] = p->g.np;
+}
+
+int ifdk_backproject_info(ifdk_plan p, int q_dtype, int64_t info[8])
+{
+    if (!p || !info) return IFDK_ERR_INVALID;
+    if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
+    fill_info(p, p->bp[q_dtype], info);
+    return IFDK_OK;
+}
+
+int ifdk_query_backproject(const ifdk_geometry *g, int q_dtype, int64_t info[10])
+{
+    if (!info) return IFDK_ERR_INVALID;
+    if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
+    int rc = validate(g);
+    if (rc != IFDK_OK) return rc;
+    ifdk_plan_s tmp;
+    rc = init_host_plan(&tmp, g);
+    if (rc != IFDK_OK) return rc;
+    plan_backproject(&tmp);
+    fill_info(&tmp, tmp.bp[q_dtype], info);
+    info[8] = tmp.bp[q_dtype].fold_w;
+    info[9] = tmp.bp[q_dtype].align;
+    return IFDK_OK;
+}
+
+}  // extern "C"

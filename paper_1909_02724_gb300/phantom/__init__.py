@@ -206,3 +206,60 @@ def workload(name: str) -> Workload:
         g = scaled_geometry(4096, 4096, 2048, nz=256)
         return Workload(name, g, 200, 1909 + 4)
     raise KeyError(name)
+
+
+# --------------------------------------------------------------------------
+# FP32 CUDA generator (phantom.cu, its own shared library) for large workloads.
+# --------------------------------------------------------------------------
+
+_gpu_lib = None
+
+
+def _load_gpu():
+    global _gpu_lib
+    if _gpu_lib is None:
+        import ctypes
+        import os
+        path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "lib",
+                            "libifdk_phantom.so")
+        if not os.path.exists(path):
+            raise RuntimeError(f"phantom generator library not built ({path})")
+        lib = ctypes.CDLL(path)
+        d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+        lib.ifdk_phantom_project.argtypes = [vp, i, d, d, i, i, d, d, d, d, vp, i, i, vp, vp]
+        lib.ifdk_phantom_project.restype = i
+        _gpu_lib = lib
+    return _gpu_lib
+
+
+def line_integrals_gpu(ell: Ellipsoids, geom: Geometry, out=None, view_begin: int = 0,
+                       view_count: int | None = None, chunk: int = 256):
+    """E (torch float32 CUDA tensor [view_count][nv][nu]) from the FP32 CUDA generator."""
+    import torch
+    n = geom.np - view_begin if view_count is None else view_count
+    if out is None:
+        out = torch.empty((n, geom.nv, geom.nu), dtype=torch.float32, device="cuda")
+    packed = np.ascontiguousarray(ell.packed())
+    angles = np.ascontiguousarray(geom.angles)
+    lib = _load_gpu()
+    stream = torch.cuda.current_stream().cuda_stream
+    for s0 in range(0, n, chunk):
+        c = min(chunk, n - s0)
+        rc = lib.ifdk_phantom_project(packed.ctypes.data, len(ell), geom.sid, geom.sdd, geom.nu, geom.nv,
+                                      geom.du, geom.dv, geom.off_u, geom.off_v, angles.ctypes.data,
+                                      view_begin + s0, c, out[s0:s0 + c].data_ptr(), stream)
+        if rc != 0:
+            raise RuntimeError(f"ifdk_phantom_project failed ({rc})")
+    return out
+
+
+def workload_projections_gpu(w: Workload, out=None):
+    """Projections of a named workload on the GPU (seeded phantom, then seeded noise)."""
+    import torch
+    E = line_integrals_gpu(w.phantom(), w.geom, out=out)
+    if w.noise:
+        gen = torch.Generator(device=E.device)
+        gen.manual_seed(w.seed)
+        sigma = w.noise * float(E.max())
+        E.add_(torch.randn(E.shape, generator=gen, device=E.device, dtype=E.dtype), alpha=sigma)
+    return E

@@ -1,0 +1,156 @@
+"""Host-side checks of the C-ABI library that need no GPU.
+
+* the library loads and exports every function include/ifdk.h declares;
+* argument validation happens before any device work;
+* the fold kernel's TMA boxes contain every tap of every thread: the kernel's
+  window and tap arithmetic is emulated (FP64 on the FP32 terms) for every
+  block and view of the parity geometries and sampled blocks of the large
+  ones, against the box sizes the library itself chooses
+  (``ifdk_query_backproject``).  This runs before any kernel touches a GPU.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1909_02724_gb300 import binding as B
+from paper_1909_02724_gb300.build import INCLUDE, LIB, build
+from paper_1909_02724_gb300.geometry import circular
+from paper_1909_02724_gb300.phantom import scaled_geometry, workload
+
+TILE, PAIRS, MARGIN = 16, 16, 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build()
+
+
+def test_exports_every_declared_symbol():
+    decl = set()
+    for f in os.listdir(INCLUDE):
+        if f.endswith(".h"):
+            txt = open(os.path.join(INCLUDE, f)).read()
+            decl |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ifdk_\w+)\s*\(", txt, re.M))
+    assert decl == set(B.EXPORTS)
+    lib = ctypes.CDLL(LIB)
+    for name in decl:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_validation():
+    assert B.status_string(B.IFDK_OK) == "ok"
+    assert "aligned" in B.status_string(B.IFDK_ERR_ALIGNMENT)
+    g = scaled_geometry(16, 16, 8)
+    bad = [g.with_(nu=0), g.with_(dx=-1.0), g.with_(sdd=500.0), g.with_(nx=2000, ny=2000),
+           g.with_(angles=np.array([np.nan] * 8))]
+    for b in bad:
+        with pytest.raises(B.IfdkError) as e:
+            B.ifdk_create(b)
+        assert e.value.code in (B.IFDK_ERR_INVALID, B.IFDK_ERR_GEOMETRY)
+
+
+def _f32(x):
+    return np.float32(x).astype(np.float64)
+
+
+def _terms(g):
+    """FP32 per-view terms as the plan forms them (FP64 closed form, cast)."""
+    cb, sb = np.cos(g.angles), np.sin(g.angles)
+    return dict(C0=_f32(g.dx * sb), C1=_f32(-g.dy * cb), C3=_f32(np.full_like(cb, g.sid)),
+                A0=_f32(g.sdd * g.dx * cb / g.du), A1=_f32(g.sdd * g.dy * sb / g.du),
+                B2=_f32(np.full_like(cb, g.sdd * g.dz / g.dv)))
+
+
+def check_fold_windows(g, q_dtype, blocks=None):
+    info = B.ifdk_query_backproject(g, q_dtype)
+    if info["path"] != 1:
+        return info
+    H, BW, FW, AL = info["box_h"], info["box_w"], info["fold_w"], info["align"]
+    t = _terms(g)
+    cx, cy, cz = (g.nx - 1) / 2, (g.ny - 1) / 2, (g.nz - 1) / 2
+    uc, vc = (g.nu - 1) / 2 + g.off_u / g.du, (g.nv - 1) / 2 + g.off_v / g.dv
+    tiles_x, tiles_y = -(-g.nx // TILE), -(-g.ny // TILE)
+    zblocks = -(-((g.nz + 1) // 2) // PAIRS)
+    if blocks is None:
+        blocks = [(bx, by, bz) for bx in range(tiles_x) for by in range(tiles_y) for bz in range(zblocks)]
+    tx, ty = np.meshgrid(np.arange(TILE), np.arange(TILE), indexing="ij")
+    tx, ty = tx.ravel(), ty.ravel()
+    p = np.arange(PAIRS)
+    V = slice(None)
+    for bx, by, bz in blocks:
+        i0, j0, k0 = bx * TILE, by * TILE, bz * PAIRS
+        kp0 = k0 - cz
+        ia, ib, ja, jb = i0 - cx, i0 + TILE - 1 - cx, j0 - cy, j0 + TILE - 1 - cy
+        ci, cj = np.array([ia, ib, ia, ib]), np.array([ja, ja, jb, jb])
+        zc = t["C0"][:, None] * ci + t["C1"][:, None] * cj + t["C3"][:, None]
+        ucn = (t["A0"][:, None] * ci + t["A1"][:, None] * cj) / zc
+        u_lo, z_lo, z_hi = ucn.min(1), zc.min(1), zc.max(1)
+        e0, e1 = t["B2"] * kp0, t["B2"] * (kp0 + PAIRS - 1)
+        v_lo = np.minimum(np.minimum(e0 / z_lo, e0 / z_hi), np.minimum(e1 / z_lo, e1 / z_hi))
+        u0f = np.floor(uc + u_lo) - MARGIN
+        u0a = np.floor(u0f / AL) * AL
+        off = u0f - u0a
+        v0 = np.floor(vc + v_lo) - MARGIN
+        assert off.min() >= 0 and (off + FW).max() <= BW - 1
+        # every thread / pair of the block (masked threads included)
+        ip = (i0 + tx) - cx
+        jp = (j0 + ty) - cy
+        z = t["C0"][V, None] * ip + t["C1"][V, None] * jp + t["C3"][V, None]
+        f = 1.0 / z
+        ul = (t["A0"][V, None] * ip + t["A1"][V, None] * jp) * f + (uc - u0f)[:, None]
+        assert ul.min() >= 0.01 and ul.max() < FW - 0.01, (bx, by, bz, ul.min(), ul.max(), FW)
+        sig = t["B2"][:, None] * f
+        vl = (vc - v0)[:, None, None] + sig[:, :, None] * (kp0 + p)[None, None, :]
+        assert vl.min() >= 0.01 and vl.max() < H - 1 - 0.01, (bx, by, bz, vl.min(), vl.max(), H)
+    return info
+
+
+@pytest.mark.parametrize("dtype", [B.IFDK_F32, B.IFDK_F16, B.IFDK_BF16])
+@pytest.mark.parametrize("geom", [
+    scaled_geometry(64, 64, 64),
+    scaled_geometry(40, 56, 24, nz=50, n_det_v=48),
+    scaled_geometry(33, 48, 16, nz=33),
+    circular(12, 64, 48, 1.5, 1.5, 37, 29, 21, 1.0, sid=1000.0, sdd=1500.0, off_u=0.6, off_v=0.75),
+    circular(10, 16, 16, 1.4, 1.3, 8, 8, 8, 1.1, 1.0, 0.9, sid=60.0, sdd=95.0, start=0.3),
+])
+def test_fold_windows_contain_every_tap(geom, dtype):
+    check_fold_windows(geom, dtype)
+
+
+@pytest.mark.parametrize("name", ["fdk512", "grad256", "fdk2048", "slab4096"])
+def test_fold_windows_large_workloads(name):
+    g = workload(name).geom
+    tiles_x, tiles_y = -(-g.nx // TILE), -(-g.ny // TILE)
+    zb = -(-((g.nz + 1) // 2) // PAIRS)
+    rng = np.random.default_rng(0)
+    blocks = {(0, 0, 0), (tiles_x - 1, tiles_y - 1, zb - 1), (tiles_x // 2, tiles_y // 2, zb // 2),
+              (0, tiles_y - 1, 0), (tiles_x - 1, 0, zb - 1)}
+    blocks |= {(int(rng.integers(tiles_x)), int(rng.integers(tiles_y)), int(rng.integers(zb))) for _ in range(6)}
+    if g.np > 512:   # subsample views for the largest scans
+        g = g.with_(angles=g.angles[::4])
+    for dt in (B.IFDK_F32, B.IFDK_F16):
+        info = check_fold_windows(g, dt, sorted(blocks))
+        assert info["path"] == 1, (name, dt, info)
+
+
+def test_general_path_for_offcentre_and_fractional_centre():
+    g = scaled_geometry(32, 48, 8)
+    assert B.ifdk_query_backproject(g, B.IFDK_F32)["path"] == 1
+    assert B.ifdk_query_backproject(g.with_(vol_off_z=1.0), B.IFDK_F32)["path"] == 0
+    assert B.ifdk_query_backproject(g.with_(off_v=0.3 * g.dv), B.IFDK_F32)["path"] == 0
+    assert B.ifdk_query_backproject(g.with_(off_v=0.5 * g.dv), B.IFDK_F32)["path"] == 1
+    assert B.ifdk_query_backproject(g.with_(nu=50), B.IFDK_F16)["path"] == 0   # rows not 16-byte multiples
+
+
+def _gpu_test_geoms():
+    import importlib
+    return importlib.import_module("tests.test_gpu_parity").GEOMS
+
+
+@pytest.mark.parametrize("dtype", [B.IFDK_F32, B.IFDK_F16, B.IFDK_BF16])
+def test_fold_windows_of_every_gpu_test_geometry(dtype):
+    for name, g in _gpu_test_geoms().items():
+        check_fold_windows(g, dtype)
