@@ -120,6 +120,12 @@ def test_fold_windows_contain_every_tap(geom, dtype):
     check_fold_windows(geom, dtype)
 
 
+@pytest.mark.parametrize("name", ["fdk64", "grad32"])
+def test_fold_windows_small_workloads(name):
+    for dt in (B.IFDK_F32, B.IFDK_F16):
+        assert check_fold_windows(workload(name).geom, dt)["path"] == 1
+
+
 @pytest.mark.parametrize("name", ["fdk512", "grad256", "fdk2048", "slab4096"])
 def test_fold_windows_large_workloads(name):
     g = workload(name).geom
