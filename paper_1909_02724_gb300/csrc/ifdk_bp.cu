@@ -1,22 +1,26 @@
 // Back-projection (Algorithm 4 of the iFDK paper) for sm_103a.
 //
-// Fold kernel (volume centred on the source plane, 2 v_c integral):
+// Mirror-pair kernels (volume centred on the source plane, 2 v_c integral):
 //   * a block owns a 16 x 16 tile of (i, j) columns and kPairs z pairs
 //     (k, nz-1-k); each thread owns one column and its z-run of pairs;
-//   * per view, the block's detector footprint is staged by TMA as two boxes,
-//     rows [v0, v0+H) (direct half) and the mirrored rows (Theorem 1:
-//     v_mirror = 2 v_c - v), in chunks of kViews views, double buffered on
-//     mbarriers; TMA's zero fill implements "taps outside the detector read 0";
-//   * the two boxes are folded into one shared-memory array whose element
-//     (m, c) holds Q[m][c], Q[2vc-m][c], Q[m][c+1], Q[2vc-m][c+1]: the direct
-//     voxel's taps at row m and its mirror's taps at the mirrored row, so one
-//     vector load serves both voxels of a pair, which share u, f and W_dis
-//     (Theorems 2, 3) and the row fraction (Theorem 1);
-//   * per (column, view) the thread forms z, f = 1/z, u, W_dis = w f^2 and the
-//     row slope once (Algorithm 4, the gray terms) and reuses them over its
-//     z-run; per pair it needs one FMA for v, one floor and the bilinear taps;
-//   * the volume accumulates in FP32 registers over all views and is written
-//     once with vectorised read-modify-write (k-major layout, 64-bit offsets).
+//   * per view, the block's detector footprint is staged by TMA as two boxes:
+//     rows [v0, v0+H) for the direct half and the mirrored rows (Theorem 1:
+//     v_mirror = 2 v_c - v), in chunks of views, double buffered on mbarriers;
+//     TMA's zero fill implements "taps outside the detector read 0";
+//   * per (column, view) a thread forms z, f = 1/z, u, W_dis = w f^2 and the row
+//     slope once (Algorithm 4, Theorems 2 and 3) and reuses them over its z-run;
+//     the pair (k, nz-1-k) shares u, f, W_dis and the row fraction (Theorem 1);
+//   * consecutive pairs step about one detector row (the magnification), so the
+//     u-interpolated taps of a row are loaded once and reused by the next pair
+//     whenever it starts on the row the previous one ended on;
+//   * direct and mirror voxel run side by side in packed f32x2 arithmetic and
+//     accumulate in FP32 registers over all views; the volume is written once
+//     (read-modify-write, vectorised, 64-bit offsets, k-major layout).
+//   FP32 storage reads the taps straight from the boxes (row pitch = 16 mod 32
+//   floats, so lanes on adjacent rows do not share banks).  FP16 / BF16
+//   storage first folds the two boxes into one array whose 8-byte element
+//   (m, c) holds Q[m][c], Q[2vc-m][c], Q[m][c+1], Q[2vc-m][c+1], so one load
+//   serves both voxels of a pair.
 // General kernel: any geometry (off-centre volume, fractional 2 v_c, large
 //   footprints, unaligned rows): Algorithm 4 without the mirror, taps read
 //   through the read-only cache with explicit bounds (zero outside).
@@ -33,10 +37,10 @@ struct ViewSmem {          // per view of a staged chunk (64 bytes)
     float A0, A1, A3, B2;
     float B3, C0, C1, C3;
     float w, uc_l, vc_l, pad;
-    int u0a, v0, v0m, off;   // box origins (u0a aligned), fold column offset inside the box
+    int u0a, v0, v0m, off;   // box origins (u0a aligned), column of the window start in the box
 };
 
-struct FoldArgs {
+struct BpArgs {
     float *vol;
     const ViewTerms *terms;
     unsigned int *status;
@@ -49,276 +53,399 @@ struct FoldArgs {
     uint32_t box_tx_bytes;     // one box, exact (TMA transaction count)
 };
 
-template <typename T> struct Fold;
-template <> struct Fold<float> {            // element = 4 x f32
-    static constexpr int ES = 16, ALIGN = 4;
+template <typename T> struct StoreT;
+template <> struct StoreT<float> {
+    static constexpr int ALIGN = 4;
     static constexpr CUtensorMapDataType TMA = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
 };
-template <> struct Fold<__half> {           // element = 4 x f16
-    static constexpr int ES = 8, ALIGN = 8;
+template <> struct StoreT<__half> {
+    static constexpr int ALIGN = 8;
     static constexpr CUtensorMapDataType TMA = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
 };
-template <> struct Fold<__nv_bfloat16> {    // element = 4 x bf16
-    static constexpr int ES = 8, ALIGN = 8;
+template <> struct StoreT<__nv_bfloat16> {
+    static constexpr int ALIGN = 8;
     static constexpr CUtensorMapDataType TMA = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
 };
 
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
-__device__ __forceinline__ float4 lds128(uint32_t a)
+__device__ __forceinline__ float lds_f32(uint32_t a)
 {
-    float4 r;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-                 : "r"(a));
+    float r;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(r) : "r"(a));
     return r;
 }
-__device__ __forceinline__ uint2 lds64(uint32_t a)
+__device__ __forceinline__ float4 lds_f32x4(uint32_t a)
+{
+    float4 r;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"(a));
+    return r;
+}
+__device__ __forceinline__ int4 lds_i32x4(uint32_t a)
+{
+    int4 r;
+    asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "r"(a));
+    return r;
+}
+__device__ __forceinline__ uint2 lds_u32x2(uint32_t a)
 {
     uint2 r;
     asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "r"(a));
     return r;
 }
-
-// Direct / mirror pair of a 2x2 tap block: (x = column c, y = column c+1).
-struct Taps { float2 x, y; };
-
-template <typename T> __device__ __forceinline__ Taps load_taps(uint32_t a);
-template <> __device__ __forceinline__ Taps load_taps<float>(uint32_t a)
+__device__ __forceinline__ uint32_t lds_u16(uint32_t a)
 {
-    const float4 e = lds128(a);
-    return {make_float2(e.x, e.y), make_float2(e.z, e.w)};
+    unsigned short r;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(r) : "r"(a));
+    return r;
 }
-template <> __device__ __forceinline__ Taps load_taps<__half>(uint32_t a)
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a)
 {
-    const uint2 e = lds64(a);
-    __half2 hx, hy;
-    *reinterpret_cast<uint32_t *>(&hx) = e.x;
-    *reinterpret_cast<uint32_t *>(&hy) = e.y;
-    return {__half22float2(hx), __half22float2(hy)};
+    uint32_t r;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r) : "r"(a));
+    return r;
 }
-template <> __device__ __forceinline__ Taps load_taps<__nv_bfloat16>(uint32_t a)
+__device__ __forceinline__ void sts_f32x4(uint32_t a, float4 v)
 {
-    const uint2 e = lds64(a);
-    return {make_float2(__uint_as_float(e.x << 16), __uint_as_float(e.x & 0xffff0000u)),
-            make_float2(__uint_as_float(e.y << 16), __uint_as_float(e.y & 0xffff0000u))};
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ void sts_i32x4(uint32_t a, int4 v)
+{
+    asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ void sts_u32x2(uint32_t a, uint2 v)
+{
+    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(v.x), "r"(v.y) : "memory");
+}
+__device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
-// Shared-memory map of the fold kernel (offsets from a 128-byte aligned base).
-constexpr uint32_t kSmemBars = 0;                 // 2 mbarriers
-constexpr uint32_t kSmemViews = 64;               // 2 x kViews ViewSmem
-constexpr uint32_t kSmemRaw = 1024;               // 2 stages x kViews x 2 boxes
-
-template <typename T, int FP>
-__global__ void __launch_bounds__(kThreads, 2)
-    bp_fold_kernel(const FoldArgs a, const __grid_constant__ CUtensorMap tmap)
+// Packed FP32 helpers (f32x2): lerp(a, b, t) = a + t (b - a), each step rounded once.
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float2 t)
 {
-    constexpr int ES = Fold<T>::ES, ALIGN = Fold<T>::ALIGN;
-    constexpr int L = kPairs;
-    constexpr uint32_t ROW = FP * ES;              // fold row pitch (bytes)
-    const int V = a.views;                         // views per chunk (<= kViews)
-    extern __shared__ unsigned char smem_dyn[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
-    ViewSmem *views = reinterpret_cast<ViewSmem *>(smem + kSmemViews);
-    unsigned char *raw = smem + kSmemRaw;
-    unsigned char *fold = raw + 2u * V * 2u * a.raw_box_bytes;
-    const uint32_t bar0 = smem_addr(smem + kSmemBars);
-    const int H = a.box_h, BW = a.box_w, FW = a.fold_w;
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    return __ffma2_rn(t, __ffma2_rn(a, m1, b), a);
+}
 
+// Shared-memory map (offsets from a 128-byte aligned base).
+constexpr uint32_t kSmemBars = 0;       // mbarrier
+constexpr uint32_t kSmemAbort = 16;     // abort flag
+constexpr uint32_t kSmemViews = 64;     // 2 slots x kViews ViewSmem (512 bytes)
+constexpr uint32_t kSmemRaw = 1024;     // one stage of views x 2 boxes, then 2 fold buffers
+
+struct Block {
+    int i0, j0, k0, i, j;
+    float ip, jp, kp0;
+};
+
+__device__ __forceinline__ Block block_coords(const BpArgs &a)
+{
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // warp = 8 x 4 patch of columns, 2 x 4 warps per 16 x 16 tile
     const int tx = (warp & 1) * 8 + (lane & 7), ty = (warp >> 1) * 4 + (lane >> 3);
-    const int i0 = (blockIdx.x % a.tiles_x) * kTileX, j0 = (blockIdx.x / a.tiles_x) * kTileY;
-    const int i = i0 + tx, j = j0 + ty;
-    const int k0 = blockIdx.y * L;
-    const float ip = (float)i - a.cx, jp = (float)j - a.cy;
-    const float kp0 = (float)k0 - a.cz;
+    Block b;
+    b.i0 = (blockIdx.x % a.tiles_x) * kTileX;
+    b.j0 = (blockIdx.x / a.tiles_x) * kTileY;
+    b.k0 = blockIdx.y * kPairs;
+    b.i = b.i0 + tx;
+    b.j = b.j0 + ty;
+    b.ip = (float)b.i - a.cx;
+    b.jp = (float)b.j - a.cy;
+    b.kp0 = (float)b.k0 - a.cz;
+    return b;
+}
+
+// Warp 0: window geometry of the nvc views of a chunk (lane v -> view v),
+// written to `slot`, then lane 0 issues the 2 boxes per view on `bar`.
+template <int ALIGN>
+__device__ __forceinline__ void stage_chunk(const BpArgs &a, const Block &b, const void *tmap, int first_view,
+                                            int nvc, uint32_t slot, uint32_t raw_stage, uint32_t bar)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane < nvc) {
+        const int s = first_view + lane;
+        const float4 *tp = reinterpret_cast<const float4 *>(a.terms + s);
+        const float4 t0 = __ldg(tp), t1 = __ldg(tp + 1), t2 = __ldg(tp + 2);
+        // t0 = (A0, A1, A3, B2), t1 = (B3, C0, C1, C3), t2 = (w, -, -, -)
+        const float ia = (float)b.i0 - a.cx, ib = ia + (kTileX - 1);
+        const float ja = (float)b.j0 - a.cy, jb = ja + (kTileY - 1);
+        float zc[4], uq[4];
+        const float ci[4] = {ia, ib, ia, ib}, cj[4] = {ja, ja, jb, jb};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            zc[q] = fmaf(t1.y, ci[q], fmaf(t1.z, cj[q], t1.w));
+            uq[q] = fmaf(t0.x, ci[q], fmaf(t0.y, cj[q], t0.z)) / zc[q];
+        }
+        const float u_lo = fminf(fminf(uq[0], uq[1]), fminf(uq[2], uq[3]));
+        const float z_lo = fminf(fminf(zc[0], zc[1]), fminf(zc[2], zc[3]));
+        const float z_hi = fmaxf(fmaxf(zc[0], zc[1]), fmaxf(zc[2], zc[3]));
+        const float e0 = fmaf(t0.w, b.kp0, t1.x), e1 = fmaf(t0.w, b.kp0 + (kPairs - 1), t1.x);
+        const float v_lo = fminf(fminf(e0 / z_lo, e0 / z_hi), fminf(e1 / z_lo, e1 / z_hi));
+        const int u0f = (int)floorf(a.uc + u_lo) - kMargin;
+        const int u0a = floor_div(u0f, ALIGN) * ALIGN;
+        const int v0 = (int)floorf(a.vc + v_lo) - kMargin;
+        const uint32_t d = slot + lane * (uint32_t)sizeof(ViewSmem);
+        sts_f32x4(d, t0);
+        sts_f32x4(d + 16, t1);
+        sts_f32x4(d + 32, make_float4(t2.x, a.uc - (float)u0f, a.vc - (float)v0, 0.0f));
+        sts_i32x4(d + 48, make_int4(u0a, v0, a.two_vc - v0 - a.box_h + 1, u0f - u0a));
+    }
+    __syncwarp();
+    if (lane == 0) {
+        mbar_arrive_expect_tx(bar, (uint32_t)nvc * 2u * a.box_tx_bytes);
+        for (int v = 0; v < nvc; ++v) {
+            const int4 o = lds_i32x4(slot + v * (uint32_t)sizeof(ViewSmem) + 48);
+            const uint32_t dst = raw_stage + 2u * v * a.raw_box_bytes;
+            tma_load_3d(dst, tmap, o.x, o.y, first_view + v, bar);
+            tma_load_3d(dst + a.raw_box_bytes, tmap, o.x, o.z, first_view + v, bar);
+        }
+    }
+}
+
+// 1/z for z > 0 (here z >= 0.1 d): hardware approximation refined by one
+// Newton-Raphson step r (2 - z r), within an ulp or so of the rounded quotient.
+__device__ __forceinline__ float rcp_nr(float z)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(z));
+    return r * fmaf(-z, r, 2.0f);
+}
+
+// Per (column, view) terms of Algorithm 4 (Theorems 2, 3).
+struct ColView {
+    float du, W, sig, vb;
+    uint32_t tu;   // floor_frac bits of u - u_window
+};
+
+__device__ __forceinline__ ColView col_view(uint32_t vs, const Block &b)
+{
+    const float4 t0 = lds_f32x4(vs), t1 = lds_f32x4(vs + 16), t2 = lds_f32x4(vs + 32);
+    ColView c;
+    const float z = fmaf(t1.y, b.ip, fmaf(t1.z, b.jp, t1.w));
+    const float f = rcp_nr(z);
+    const float x = fmaf(t0.x, b.ip, fmaf(t0.y, b.jp, t0.z));
+    const float ul = fmaf(x, f, t2.y);
+    c.tu = floor_frac(ul, c.du);
+    c.W = t2.x * f * f;
+    c.sig = t0.w * f;
+    c.vb = fmaf(c.sig, b.kp0, fmaf(t1.x, f, t2.z));
+    return c;
+}
+
+// Writes the thread's z-run: acc[p].x -> voxel k0+p, acc[p].y -> its mirror nz-1-k0-p.
+__device__ __forceinline__ void write_run(const BpArgs &a, const Block &b, const float2 *acc)
+{
+    constexpr int L = kPairs;
+    if (b.i >= a.nx || b.j >= a.ny) return;
+    float *col = a.vol + ((size_t)b.i * a.ny + b.j) * (size_t)a.nz;
+    const int half = a.nz / 2, npairs = (a.nz + 1) / 2;
+    if ((a.nz & 3) == 0 && b.k0 + L <= half) {
+        float4 *pd = reinterpret_cast<float4 *>(col + b.k0);
+        float4 *pm = reinterpret_cast<float4 *>(col + (a.nz - b.k0 - L));
+#pragma unroll
+        for (int q = 0; q < L / 4; ++q) {
+            float4 d = pd[q];
+            d.x += acc[4 * q].x; d.y += acc[4 * q + 1].x; d.z += acc[4 * q + 2].x; d.w += acc[4 * q + 3].x;
+            pd[q] = d;
+            float4 m = pm[q];   // voxels nz-k0-L+4q .. +3 mirror pairs L-1-4q .. L-4-4q
+            m.x += acc[L - 1 - 4 * q].y; m.y += acc[L - 2 - 4 * q].y;
+            m.z += acc[L - 3 - 4 * q].y; m.w += acc[L - 4 - 4 * q].y;
+            pm[q] = m;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < L; ++p) {
+            const int k = b.k0 + p;
+            if (k < npairs) {
+                col[k] += acc[p].x;
+                const int km = a.nz - 1 - k;
+                if (km > k) col[km] += acc[p].y;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fold kernel (any storage type): the two boxes are folded into one array
+// whose element (m, c) holds Q[m][c], Q[2vc-m][c], Q[m][c+1], Q[2vc-m][c+1]
+// (direct and mirror row, two columns): one vector load per row serves both
+// voxels of a pair.  Branch-free pair loop: two row loads per pair.
+template <typename T> struct FoldElem;
+template <> struct FoldElem<float> {
+    static constexpr int ES = 16;
+    __device__ __forceinline__ static void load(uint32_t a, float2 &x, float2 &y)
+    {
+        const float4 e = lds_f32x4(a);
+        x = make_float2(e.x, e.y);
+        y = make_float2(e.z, e.w);
+    }
+};
+template <> struct FoldElem<__half> {
+    static constexpr int ES = 8;
+    __device__ __forceinline__ static void load(uint32_t a, float2 &x, float2 &y)
+    {
+        const uint2 e = lds_u32x2(a);
+        __half2 hx, hy;
+        *reinterpret_cast<uint32_t *>(&hx) = e.x;
+        *reinterpret_cast<uint32_t *>(&hy) = e.y;
+        x = __half22float2(hx);
+        y = __half22float2(hy);
+    }
+};
+template <> struct FoldElem<__nv_bfloat16> {
+    static constexpr int ES = 8;
+    __device__ __forceinline__ static void load(uint32_t a, float2 &x, float2 &y)
+    {
+        const uint2 e = lds_u32x2(a);
+        x = make_float2(__uint_as_float(e.x << 16), __uint_as_float(e.x & 0xffff0000u));
+        y = make_float2(__uint_as_float(e.y << 16), __uint_as_float(e.y & 0xffff0000u));
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ float2 fold_row(uint32_t a, float2 du2)
+{
+    float2 x, y;
+    FoldElem<T>::load(a, x, y);
+    return lerp2(x, y, du2);
+}
+
+// The z-run of one (column, view): pair p samples rows n_p, n_p + 1 at
+// v_p = vb + p sig (window coordinates).  With REUSE (every lane of the warp
+// has sig < 1, so n_{p+1} - n_p is 0 or 1) each pair loads only row n_p + 1
+// and takes row n_p from the previous pair's upper row when it moved up;
+// otherwise both rows are loaded.  Both forms are branch-free.
+template <typename T, int ES, uint32_t ROW, bool REUSE>
+__device__ __forceinline__ void pair_loop(float2 *acc, uint32_t base, float sig, float vb, float2 du2, float2 W2)
+{
+    constexpr int L = kPairs;
+    float dv;
+    uint32_t tv = floor_frac(vb, dv);
+    uint32_t ad = base + tv * ROW;
+    float2 lo = fold_row<T>(ad, du2), hi = fold_row<T>(ad + ROW, du2);
+    acc[0] = __ffma2_rn(W2, lerp2(lo, hi, make_float2(dv, dv)), acc[0]);
+#pragma unroll
+    for (int p = 1; p < L; ++p) {
+        const uint32_t tn = floor_frac(fmaf((float)p, sig, vb), dv);
+        ad = base + tn * ROW;
+        if constexpr (REUSE) {
+            const bool moved = tn != tv;
+            tv = tn;
+            const float2 hn = fold_row<T>(ad + ROW, du2);
+            lo = moved ? hi : lo;
+            hi = hn;
+        } else {
+            lo = fold_row<T>(ad, du2);
+            hi = fold_row<T>(ad + ROW, du2);
+        }
+        acc[p] = __ffma2_rn(W2, lerp2(lo, hi, make_float2(dv, dv)), acc[p]);
+    }
+}
+
+template <typename T, int FP>
+__global__ void __launch_bounds__(kThreads, 3)
+    bp_pairs_fold_kernel(const BpArgs a, const __grid_constant__ CUtensorMap tmap)
+{
+    constexpr int ES = FoldElem<T>::ES, ALIGN = StoreT<T>::ALIGN;
+    constexpr uint32_t ROW = FP * ES;   // fold row pitch, bytes
+    constexpr uint32_t VS = kViews * sizeof(ViewSmem);
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    const uint32_t sbase = smem_addr(smem_dyn);
+    const uint32_t s0 = sbase + ((128u - (sbase & 127u)) & 127u);
+    const uint32_t bar = s0 + kSmemBars, views0 = s0 + kSmemViews, raw = s0 + kSmemRaw;
+    const int V = a.views, H = a.box_h, BW = a.box_w, FW = a.fold_w;
+    const uint32_t fold0 = raw + 2u * V * a.raw_box_bytes;   // one raw stage, then two fold buffers
+    const uint32_t fold_bytes = (uint32_t)V * H * ROW;
+    const Block b = block_coords(a);
+    const int tid = threadIdx.x, warp = tid >> 5;
 
     if (tid == 0) {
         prefetch_tmap(&tmap);
-        mbar_init(bar0, 1);
-        mbar_init(bar0 + 8, 1);
+        mbar_init(bar, 1);
+        sts_u32(s0 + kSmemAbort, 0u);
         fence_barrier_init();
     }
     __syncthreads();
 
     const int nchunks = (a.view_count + V - 1) / V;
-
-    // Warp 0: geometry of chunk cn (lane v -> view v) and its TMA issue.
-    auto stage_chunk = [&](int cn) {
-        const int st = cn & 1;
+    // chunk cn uses view slot cn & 1, the raw stage, and mbarrier phase cn
+    auto stage = [&](int cn) {
+        stage_chunk<ALIGN>(a, b, &tmap, a.view_begin + cn * V, min(V, a.view_count - cn * V),
+                           views0 + (cn & 1) * VS, raw, bar);
+    };
+    // wait for chunk cn's boxes, then fold them into buffer cn & 1 (warp = row
+    // group, lane = column: conflict-free loads and stores, no divisions)
+    auto fold_chunk = [&](int cn) {
+        if (!mbar_wait_bounded(bar, cn & 1, a.wait_ns)) sts_u32(s0 + kSmemAbort, 1u);
         const int nvc = min(V, a.view_count - cn * V);
-        if (lane < nvc) {
-            const int s = a.view_begin + cn * V + lane;
-            const float4 *tp = reinterpret_cast<const float4 *>(a.terms + s);
-            const float4 t0 = __ldg(tp), t1 = __ldg(tp + 1), t2 = __ldg(tp + 2);
-            // t0 = (A0, A1, A3, B2), t1 = (B3, C0, C1, C3), t2 = (w, -, -, -)
-            const float ia = (float)i0 - a.cx, ib = ia + (kTileX - 1);
-            const float ja = (float)j0 - a.cy, jb = ja + (kTileY - 1);
-            float zc[4], uc[4];
-            const float ci[4] = {ia, ib, ia, ib}, cj[4] = {ja, ja, jb, jb};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                zc[q] = fmaf(t1.y, ci[q], fmaf(t1.z, cj[q], t1.w));
-                uc[q] = fmaf(t0.x, ci[q], fmaf(t0.y, cj[q], t0.z)) / zc[q];
-            }
-            const float u_lo = fminf(fminf(uc[0], uc[1]), fminf(uc[2], uc[3]));
-            const float z_lo = fminf(fminf(zc[0], zc[1]), fminf(zc[2], zc[3]));
-            const float z_hi = fmaxf(fmaxf(zc[0], zc[1]), fmaxf(zc[2], zc[3]));
-            const float ka = kp0, kb = kp0 + (L - 1);
-            const float e0 = fmaf(t0.w, ka, t1.x), e1 = fmaf(t0.w, kb, t1.x);
-            const float v_lo = fminf(fminf(e0 / z_lo, e0 / z_hi), fminf(e1 / z_lo, e1 / z_hi));
-            const int u0f = (int)floorf(a.uc + u_lo) - kMargin;
-            const int u0a = floor_div(u0f, ALIGN) * ALIGN;
-            const int v0 = (int)floorf(a.vc + v_lo) - kMargin;
-            ViewSmem &vs = views[st * V + lane];
-            vs.A0 = t0.x; vs.A1 = t0.y; vs.A3 = t0.z; vs.B2 = t0.w;
-            vs.B3 = t1.x; vs.C0 = t1.y; vs.C1 = t1.z; vs.C3 = t1.w;
-            vs.w = t2.x;
-            vs.uc_l = a.uc - (float)u0f;
-            vs.vc_l = a.vc - (float)v0;
-            vs.pad = 0.0f;
-            vs.u0a = u0a;
-            vs.v0 = v0;
-            vs.v0m = a.two_vc - v0 - H + 1;
-            vs.off = u0f - u0a;
-        }
-        __syncwarp();
-        if (lane == 0) {
-            const uint32_t bar = bar0 + 8 * st;
-            mbar_arrive_expect_tx(bar, (uint32_t)nvc * 2u * a.box_tx_bytes);
-            for (int v = 0; v < nvc; ++v) {
-                const ViewSmem &vs = views[st * V + v];
-                const int s = a.view_begin + cn * V + v;
-                const uint32_t dst = smem_addr(raw + ((st * V + v) * 2u) * a.raw_box_bytes);
-                tma_load_3d(dst, &tmap, vs.u0a, vs.v0, s, bar);
-                tma_load_3d(dst + a.raw_box_bytes, &tmap, vs.u0a, vs.v0m, s, bar);
+        const uint32_t fbuf = fold0 + (cn & 1) * fold_bytes, vslot = views0 + (cn & 1) * VS;
+        const int lane = tid & 31, rgrp = tid >> 5;
+        for (int v = 0; v < nvc; ++v) {
+            const int off = lds_i32x4(vslot + v * sizeof(ViewSmem) + 48).w;
+            const uint32_t rdv = raw + 2u * v * a.raw_box_bytes, rmv = rdv + a.raw_box_bytes;
+            const uint32_t fv = fbuf + (uint32_t)v * H * ROW;
+            for (int m = rgrp; m < H; m += kThreads / 32) {
+                const uint32_t rdm = rdv + (uint32_t)(m * BW + off) * sizeof(T);
+                const uint32_t rmm = rmv + (uint32_t)((H - 1 - m) * BW + off) * sizeof(T);
+                for (int cc = lane; cc < FW; cc += 32) {
+                    const uint32_t rd = rdm + cc * sizeof(T), rm = rmm + cc * sizeof(T);
+                    const uint32_t fa = fv + m * ROW + cc * ES;
+                    if constexpr (sizeof(T) == 4) {
+                        sts_f32x4(fa, make_float4(lds_f32(rd), lds_f32(rm), lds_f32(rd + 4), lds_f32(rm + 4)));
+                    } else {
+                        const uint32_t p0 = lds_u16(rd) | (lds_u16(rm) << 16);
+                        const uint32_t p1 = lds_u16(rd + 2) | (lds_u16(rm + 2) << 16);
+                        sts_u32x2(fa, make_uint2(p0, p1));
+                    }
+                }
             }
         }
     };
 
-    if (warp == 0) stage_chunk(0);
+    if (warp == 0) stage(0);
+    fold_chunk(0);
+    __syncthreads();
 
-    float2 acc[L];
+    float2 acc[kPairs];
 #pragma unroll
-    for (int p = 0; p < L; ++p) acc[p] = make_float2(0.0f, 0.0f);
+    for (int p = 0; p < kPairs; ++p) acc[p] = make_float2(0.0f, 0.0f);
 
-    const int nseg = (FW + 7) / 8;
-    bool failed = false;
+    bool aborted = lds_u32(s0 + kSmemAbort) != 0;
     int c = 0;
-    for (; c < nchunks; ++c) {
-        const int st = c & 1;
+    for (; c < nchunks && !aborted; ++c) {
+        // the raw stage was folded in the previous iteration: refill it with chunk c+1
+        if (warp == 0 && c + 1 < nchunks) stage(c + 1);
         const int nvc = min(V, a.view_count - c * V);
-        if (warp == 0 && c + 1 < nchunks) stage_chunk(c + 1);
-        const bool ok = mbar_wait_bounded(bar0 + 8 * st, (c >> 1) & 1, a.wait_ns);
-        if (__syncthreads_or(!ok)) { failed = true; break; }
-
-        // Fold the raw boxes of this chunk: F[m][c] = (D[m][c], M[H-1-m][c], D[m][c+1], M[H-1-m][c+1]).
-        for (int item = tid; item < nvc * H * nseg; item += kThreads) {
-            const int v = item / (H * nseg), rem = item - v * (H * nseg);
-            const int m = rem / nseg, seg = rem - m * nseg;
-            const int off = views[st * V + v].off;
-            const T *rd = reinterpret_cast<const T *>(raw + ((st * V + v) * 2u) * a.raw_box_bytes) + m * BW + off;
-            const T *rm = reinterpret_cast<const T *>(raw + ((st * V + v) * 2u + 1u) * a.raw_box_bytes) +
-                          (H - 1 - m) * BW + off;
-            unsigned char *frow = fold + (size_t)(v * H + m) * ROW;
-            const int cb = seg * 8, ce = min(FW, cb + 8);
-            if constexpr (sizeof(T) == 4) {
-                float d0 = rd[cb], m0 = rm[cb];
-                for (int cc = cb; cc < ce; ++cc) {
-                    const float d1 = rd[cc + 1], m1 = rm[cc + 1];
-                    *reinterpret_cast<float4 *>(frow + cc * ES) = make_float4(d0, m0, d1, m1);
-                    d0 = d1;
-                    m0 = m1;
-                }
-            } else {
-                const uint16_t *rd16 = reinterpret_cast<const uint16_t *>(rd);
-                const uint16_t *rm16 = reinterpret_cast<const uint16_t *>(rm);
-                uint32_t p0 = (uint32_t)rd16[cb] | ((uint32_t)rm16[cb] << 16);
-                for (int cc = cb; cc < ce; ++cc) {
-                    const uint32_t p1 = (uint32_t)rd16[cc + 1] | ((uint32_t)rm16[cc + 1] << 16);
-                    *reinterpret_cast<uint2 *>(frow + cc * ES) = make_uint2(p0, p1);
-                    p0 = p1;
-                }
-            }
-        }
-        __syncthreads();
-
-        const uint32_t fold0 = smem_addr(fold);
+        const uint32_t vslot = views0 + (c & 1) * VS, fbuf = fold0 + (c & 1) * fold_bytes;
         for (int v = 0; v < nvc; ++v) {
-            const ViewSmem &vs = views[st * V + v];
-            const float z = fmaf(vs.C0, ip, fmaf(vs.C1, jp, vs.C3));
-            const float f = __frcp_rn(z);
-            const float x = fmaf(vs.A0, ip, fmaf(vs.A1, jp, vs.A3));
-            const float ul = fmaf(x, f, vs.uc_l);
-            float du;
-            const uint32_t tu = floor_frac(ul, du);
-            const float W = vs.w * f * f;
-            const float sig = vs.B2 * f;
-            const float vb = fmaf(sig, kp0, fmaf(vs.B3, f, vs.vc_l));
-            // address of fold element (n, cu) = base + bits(t_v) * ROW, n = bits(t_v) - 2^23 bias
-            const uint32_t base = fold0 + (uint32_t)v * (uint32_t)H * ROW + (tu - kFloorBias) * ES -
-                                  kFloorBias * ROW;
-#pragma unroll
-            for (int p = 0; p < L; ++p) {
-                const float vl = fmaf((float)p, sig, vb);
-                float dv;
-                const uint32_t tv = floor_frac(vl, dv);
-                const uint32_t ad = base + tv * ROW;
-                const Taps lo = load_taps<T>(ad), hi = load_taps<T>(ad + ROW);
-                const float lx = fmaf(du, lo.y.x - lo.x.x, lo.x.x);   // direct, row n
-                const float ly = fmaf(du, lo.y.y - lo.x.y, lo.x.y);   // mirror, row 2vc-n
-                const float hx = fmaf(du, hi.y.x - hi.x.x, hi.x.x);   // direct, row n+1
-                const float hy = fmaf(du, hi.y.y - hi.x.y, hi.x.y);   // mirror, row 2vc-n-1
-                acc[p].x = fmaf(W, fmaf(dv, hx - lx, lx), acc[p].x);
-                acc[p].y = fmaf(W, fmaf(dv, hy - ly, ly), acc[p].y);
-            }
+            const ColView cv = col_view(vslot + v * sizeof(ViewSmem), b);
+            // element (n, cu) = base + bits(t_v) * ROW, n = bits(t_v) - bias
+            const uint32_t base = fbuf + (uint32_t)v * H * ROW + (cv.tu - kFloorBias) * ES - kFloorBias * ROW;
+            const float2 du2 = make_float2(cv.du, cv.du), W2 = make_float2(cv.W, cv.W);
+            // sig < 1 - 2^-10 keeps fp32 rounding of v_{p+1} - v_p below one row
+            if (__all_sync(0xffffffffu, cv.sig < 0.9990234375f))
+                pair_loop<T, ES, ROW, true>(acc, base, cv.sig, cv.vb, du2, W2);
+            else
+                pair_loop<T, ES, ROW, false>(acc, base, cv.sig, cv.vb, du2, W2);
         }
+        if (c + 1 < nchunks) fold_chunk(c + 1);
         __syncthreads();
+        aborted = lds_u32(s0 + kSmemAbort) != 0;
     }
-
-    if (failed) {
-        // Record the timeout, then keep the block's shared memory alive until
-        // every TMA copy it issued has landed (bounded again), and leave the
-        // volume untouched.
+    if (aborted) {
+        // record the timeout; keep shared memory alive until the one copy that may
+        // still be in flight (chunk c, issued before the failing wait) has landed
         if (tid == 0) {
             atomicOr(a.status, kStatusTimeout);
-            mbar_wait_bounded(bar0 + 8 * (c & 1), (c >> 1) & 1, a.wait_ns);
-            if (c + 1 < nchunks)
-                mbar_wait_bounded(bar0 + 8 * ((c + 1) & 1), ((c + 1) >> 1) & 1, a.wait_ns);
+            if (c < nchunks) mbar_wait_bounded(bar, c & 1, a.wait_ns);
         }
         return;
     }
-
-    if (i < a.nx && j < a.ny) {
-        float *col = a.vol + ((size_t)i * a.ny + j) * (size_t)a.nz;
-        const int half = a.nz / 2, npairs = (a.nz + 1) / 2;
-        if ((a.nz & 3) == 0 && k0 + L <= half) {
-            float4 *pd = reinterpret_cast<float4 *>(col + k0);
-            float4 *pm = reinterpret_cast<float4 *>(col + (a.nz - k0 - L));
-#pragma unroll
-            for (int q = 0; q < L / 4; ++q) {
-                float4 d = pd[q];
-                d.x += acc[4 * q].x; d.y += acc[4 * q + 1].x; d.z += acc[4 * q + 2].x; d.w += acc[4 * q + 3].x;
-                pd[q] = d;
-                float4 m = pm[q];   // voxels nz-k0-L+4q .. +3 are mirrors of pairs L-1-4q .. L-4-4q
-                m.x += acc[L - 1 - 4 * q].y; m.y += acc[L - 2 - 4 * q].y;
-                m.z += acc[L - 3 - 4 * q].y; m.w += acc[L - 4 - 4 * q].y;
-                pm[q] = m;
-            }
-        } else {
-#pragma unroll
-            for (int p = 0; p < L; ++p) {
-                const int k = k0 + p;
-                if (k < npairs) {
-                    col[k] += acc[p].x;
-                    const int km = a.nz - 1 - k;
-                    if (km > k) col[km] += acc[p].y;
-                }
-            }
-        }
-    }
+    write_run(a, b, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -385,9 +512,9 @@ __global__ void __launch_bounds__(kThreads) bp_general_kernel(const GenArgs a)
         if (kb + zz < a.nz) col[kb + zz] += acc[zz];
 }
 
-// Host-side sizing of the fold kernel's TMA boxes: analytic FP64 bounds of
+// Host-side sizing of the pair kernels' TMA boxes: analytic FP64 bounds of
 // the largest detector footprint of any block over any view.
-BpLaunch size_fold(const ifdk_plan_s *p, int q_dtype)
+BpLaunch size_pairs(const ifdk_plan_s *p, int q_dtype)
 {
     const ifdk_geometry &g = p->g;
     BpLaunch b{};
@@ -411,26 +538,27 @@ BpLaunch size_fold(const ifdk_plan_s *p, int q_dtype)
     const double b2 = g.sdd * g.dz / g.dv;
     const double hv = b2 * (kPairs - 1) / cmin + b2 * kmax * et / (cmin * cmin);
     b.fold_w = (int)std::ceil(wu) + 2 * kMargin + 2;
-    b.box_w = ((b.fold_w + 1 + b.align - 1) + b.align - 1) / b.align * b.align;
+    const int need_w = b.fold_w + b.align;   // the window starts up to align-1 into the box
     b.box_h = (int)std::ceil(hv) + 2 * kMargin + 3;
+    b.box_w = (need_w + b.align - 1) / b.align * b.align;
     b.pitch = b.fold_w <= kFoldPitchS - 1 ? kFoldPitchS : kFoldPitchL;
-    const int fes = q_dtype == IFDK_F32 ? 16 : 8;
+    if (b.fold_w > kFoldPitchL - 1 || b.box_w > 256 || b.box_h > 256) return b;
     const size_t box_bytes = ((size_t)b.box_w * b.box_h * es + 127) / 128 * 128;
-    // the most views per chunk that keep two blocks per SM (else one)
+    // the most views per chunk that keep three blocks (80 registers each) per SM
+    const int fes = q_dtype == IFDK_F32 ? 16 : 8;
     for (b.views = kViews; b.views >= 1; --b.views) {
-        b.smem = 128 + kSmemRaw + 2 * b.views * 2 * box_bytes + (size_t)b.views * b.box_h * b.pitch * fes;
-        if (b.smem <= 112 * 1024 || b.views == 1) break;
+        b.smem = 128 + kSmemRaw + (size_t)b.views * 2 * box_bytes;      // one raw stage
+        b.smem += 2 * (size_t)b.views * b.box_h * b.pitch * fes;        // two fold buffers
+        if (b.smem <= 74 * 1024 || b.views == 1) break;   // three blocks per SM
     }
-    if (b.fold_w > kFoldPitchL - 1 || b.box_w > 256 || b.box_h > 256 || b.smem > 220 * 1024 ||
-        (size_t)g.np * g.nv * g.nu * es >= ((size_t)1 << 40) || zblocks > 65535)
-        return b;
+    if (b.smem > 220 * 1024 || (size_t)g.np * g.nv * g.nu * es >= ((size_t)1 << 40) || zblocks > 65535) return b;
     b.path = 1;
     return b;
 }
 
 template <typename T>
-int launch_fold(ifdk_plan_s *p, const BpLaunch &b, const void *Q, int view_begin, int view_count,
-                float *vol, cudaStream_t stream)
+int launch_pairs(ifdk_plan_s *p, const BpLaunch &b, const void *Q, int view_begin, int view_count, float *vol,
+                 cudaStream_t stream)
 {
     const ifdk_geometry &g = p->g;
     EncodeTiledFn enc = encode_tiled();
@@ -441,11 +569,11 @@ int launch_fold(ifdk_plan_s *p, const BpLaunch &b, const void *Q, int view_begin
     const cuuint64_t strides[2] = {(cuuint64_t)g.nu * es, (cuuint64_t)g.nu * g.nv * es};
     const cuuint32_t box[3] = {(cuuint32_t)b.box_w, (cuuint32_t)b.box_h, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    if (enc(&tmap, Fold<T>::TMA, 3, const_cast<void *>(Q), dims, strides, box, estr,
+    if (enc(&tmap, StoreT<T>::TMA, 3, const_cast<void *>(Q), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return IFDK_ERR_CUDA;
-    FoldArgs a;
+    BpArgs a;
     a.vol = vol;
     a.terms = p->d_terms;
     a.status = p->d_status;
@@ -461,7 +589,8 @@ int launch_fold(ifdk_plan_s *p, const BpLaunch &b, const void *Q, int view_begin
     a.uc = (float)p->uc; a.vc = (float)p->vc;
     a.box_tx_bytes = (uint32_t)(b.box_w * b.box_h * es);
     a.raw_box_bytes = (a.box_tx_bytes + 127u) / 128u * 128u;
-    auto kern = b.pitch == kFoldPitchS ? bp_fold_kernel<T, kFoldPitchS> : bp_fold_kernel<T, kFoldPitchL>;
+    void (*kern)(const BpArgs, const CUtensorMap);
+    kern = b.pitch == kFoldPitchS ? bp_pairs_fold_kernel<T, kFoldPitchS> : bp_pairs_fold_kernel<T, kFoldPitchL>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem) != cudaSuccess)
         return IFDK_ERR_CUDA;
     kern<<<dim3(b.grid_x, b.grid_y), kThreads, b.smem, stream>>>(a, tmap);
@@ -492,7 +621,7 @@ int launch_general(ifdk_plan_s *p, const void *Q, int view_begin, int view_count
 void plan_backproject(ifdk_plan_s *p)
 {
     for (int t = 0; t < 3; ++t) {
-        p->bp[t] = size_fold(p, t);
+        p->bp[t] = size_pairs(p, t);
         if (!p->bp[t].path) {   // general kernel grid
             p->bp[t].grid_x = ((p->g.nx + kTileX - 1) / kTileX) * ((p->g.ny + kTileY - 1) / kTileY);
             p->bp[t].grid_y = (p->g.nz + kGenZ - 1) / kGenZ;
@@ -509,9 +638,9 @@ int launch_backproject(ifdk_plan_s *p, const void *Q, int q_dtype, int view_begi
     const BpLaunch &b = p->bp[q_dtype];
     if (b.path == 1) {
         switch (q_dtype) {
-        case IFDK_F32: return launch_fold<float>(p, b, Q, view_begin, view_count, vol, stream);
-        case IFDK_F16: return launch_fold<__half>(p, b, Q, view_begin, view_count, vol, stream);
-        default: return launch_fold<__nv_bfloat16>(p, b, Q, view_begin, view_count, vol, stream);
+        case IFDK_F32: return launch_pairs<float>(p, b, Q, view_begin, view_count, vol, stream);
+        case IFDK_F16: return launch_pairs<__half>(p, b, Q, view_begin, view_count, vol, stream);
+        default: return launch_pairs<__nv_bfloat16>(p, b, Q, view_begin, view_count, vol, stream);
         }
     }
     switch (q_dtype) {

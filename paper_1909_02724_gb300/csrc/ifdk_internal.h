@@ -28,8 +28,8 @@ struct ViewTerms {
 constexpr int kTileX = 16, kTileY = 16, kThreads = kTileX * kTileY;
 constexpr int kPairs = 16;       // z pairs per thread (the thread's z-run)
 constexpr int kViews = 4;        // max views per shared-memory chunk
-constexpr int kFoldPitchS = 33;  // fold row pitch (elements, odd: spreads banks) for widths <= 32
-constexpr int kFoldPitchL = 49;  // ... and for widths <= 48
+constexpr int kFoldPitchS = 36;  // fold row pitch (elements; 4 mod 8 spreads banks) for widths <= 35
+constexpr int kFoldPitchL = 52;  // ... and for widths <= 51
 constexpr int kMargin = 1;       // window margin (pixels) on every side
 constexpr int kGenZ = 16;        // z voxels per thread in the general kernel
 

@@ -119,7 +119,7 @@ def test_unrolled_gd_grad_vs_fd(setup):
     loss.backward()
     grad = at.grad.double().cpu().numpy()
     l0 = _oracle_unrolled_loss(g, y, x0, alphas)
-    assert abs(float(loss) - l0) <= 1e-4 * l0
+    assert abs(float(loss.detach()) - l0) <= 1e-4 * l0
     fd = []
     check = [0, 5, 12, 19]
     for t in check:
@@ -131,9 +131,12 @@ def test_unrolled_gd_grad_vs_fd(setup):
     assert rel(grad[check], np.array(fd)) <= 1e-4
 
 
-def test_unrolled_gd_recompute_saves_memory():
-    """grad256 workload (256^3, 360 views of 384^2): 20 steps; recomputation keeps
-    the peak below storing every step, and the data misfit decreases."""
+def test_unrolled_gd_recompute_memory_and_gradients():
+    """grad256 workload (256^3, 360 views of 384^2), 20 unrolled steps.  The linear
+    operators save no tensors, so with per-step recomputation each step keeps only
+    its input volume: the peak stays within 20 volumes plus a constant working set
+    (no projection-sized tensor is kept per step); gradients equal the stored-graph
+    run and the data misfit decreases."""
     from paper_1909_02724_gb300 import autograd as A
     from paper_1909_02724_gb300.binding import Plan
     from paper_1909_02724_gb300.phantom import workload_projections_gpu
@@ -147,7 +150,8 @@ def test_unrolled_gd_recompute_saves_memory():
         v = plan.backproject(plan.project(v))
         lam = float(v.norm())
         v /= lam
-    peaks, losses = {}, {}
+    vol_b, proj_b = 4 * g.nx * g.ny * g.nz, 4 * g.np * g.nv * g.nu
+    peaks, losses, grads = {}, {}, {}
     for recompute in (True, False):
         torch.cuda.synchronize()
         torch.cuda.reset_peak_memory_stats()
@@ -159,8 +163,10 @@ def test_unrolled_gd_recompute_saves_memory():
         loss.backward()
         torch.cuda.synchronize()
         peaks[recompute] = torch.cuda.max_memory_allocated() - base
-        losses[recompute] = float(loss)
-        assert torch.isfinite(alphas.grad).all()
-    assert peaks[True] < 0.5 * peaks[False], peaks
-    assert abs(losses[True] - losses[False]) <= 1e-4 * losses[False]
-    assert losses[True] < float((y * y).sum())
+        losses[recompute] = float(loss.detach())
+        grads[recompute] = alphas.grad.detach().double().cpu().numpy()
+        assert np.isfinite(grads[recompute]).all()
+    assert peaks[True] <= 20 * vol_b + 4 * (vol_b + proj_b), (peaks, vol_b, proj_b)
+    assert abs(losses[True] - losses[False]) <= 1e-5 * losses[False]
+    assert rel(grads[True], grads[False]) <= 1e-5
+    assert losses[True] < 0.5 * float((y * y).sum())
