@@ -257,10 +257,11 @@ def run_ours(args):
     ms_per_step = ms / args.steps
     value = world * g.updates * args.steps / (ms * 1e-3) / 2 ** 30
 
-    # launches of our kernels per step: filter (whole views per launch, <= 65535*4 rows) + 1 back-projection
+    # launches of our kernels per step: tensor-core filter (a split pre-pass and a GEMM per
+    # chunk of up to 16384 rows, the preferred workspace) + 1 back-projection
     rows = g.np * g.nv
-    chunk = (65535 * 4 // g.nv) * g.nv
-    launches = (-(-rows // chunk) + 1) * args.steps
+    cap = min(16384, -(-rows // 128) * 128)
+    launches = (2 * -(-rows // cap) + 1) * args.steps
 
     # end to end through host buffers (pinned), copies inside the timed region
     e2e = None

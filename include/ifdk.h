@@ -94,13 +94,26 @@ int ifdk_destroy(ifdk_plan p);
 
 /* Filtering stage, Algorithm 1: Q[s][v][n] = sum_m h(n-m) F_cos[v][m] E[s][v][m]
    for the np views: the cosine weight followed by an exact linear (zero-padded)
-   Ram-Lak convolution of every detector row.
-   E: device FP32 [np][nv][nu], read only.  Q: device [np][nv][nu] of q_dtype
-   (IFDK_F32, IFDK_F16 or IFDK_BF16), overwritten.  split_terms selects the
-   operand precision of the tensor-core Toeplitz product (1..3 BF16 terms per
-   operand); 0 selects the FP32 SIMT kernel.  E and Q must not overlap. */
+   Ram-Lak convolution of every detector row, computed as a dense Toeplitz
+   product (the convolution theorem of Sec. 2.2.3 is not used).
+   E: device FP32 [np][nv][nu], read only, 16-byte aligned.  Q: device
+   [np][nv][nu] of q_dtype (IFDK_F32, IFDK_F16 or IFDK_BF16), overwritten,
+   16-byte aligned.  E and Q must not overlap.
+   split_terms = 1..3: tensor cores (tcgen05, BF16 operands each split into
+   that many terms, FP32 accumulation); 3 keeps FP32 accuracy, 2 suits 16-bit
+   storage.  It needs a device workspace of at least the minimum that
+   ifdk_filter_workspace_size reports, 128-byte aligned, owned by the caller
+   and not used by anything else until the call's work has run (larger
+   workspaces process more rows per launch).  split_terms = 0: FP32 SIMT
+   kernel, workspace ignored (may be NULL). */
 int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms,
-                void *stream);
+                void *workspace, size_t workspace_bytes, void *stream);
+
+/* Workspace of ifdk_filter for split_terms: the minimum (one 128-row tile of
+   split operands) and a preferred size (up to 16384 rows per launch).  Either
+   pointer may be NULL.  0 bytes for split_terms = 0. */
+int ifdk_filter_workspace_size(ifdk_plan p, int split_terms, size_t *min_bytes,
+                               size_t *preferred_bytes);
 
 /* Adjoint of ifdk_filter for FP32 (the Toeplitz matrix is symmetric because h
    is even, and F_cos is diagonal): G_E[s][v][m] = F_cos[v][m] sum_n h(n-m) G_Q[s][v][n].

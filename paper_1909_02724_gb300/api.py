@@ -13,7 +13,7 @@ from .binding import Plan
 
 
 def fdk(plan: Plan, E: torch.Tensor, vol: torch.Tensor | None = None, Q: torch.Tensor | None = None,
-        dtype=torch.float32, split_terms: int = 0, stream=None) -> torch.Tensor:
+        dtype=torch.float32, split_terms: int | None = None, stream=None) -> torch.Tensor:
     """FDK on the device: vol (+)= backproject(filter(E)).  E: float32 CUDA [np][nv][nu].
 
     Q (optional): workspace for the filtered views, of the storage dtype.
@@ -28,7 +28,8 @@ def fdk(plan: Plan, E: torch.Tensor, vol: torch.Tensor | None = None, Q: torch.T
 
 
 def fdk_host(plan: Plan, E_host: torch.Tensor, vol_host: torch.Tensor, E_dev: torch.Tensor,
-             Q_dev: torch.Tensor, vol_dev: torch.Tensor, split_terms: int = 0, stream=None) -> torch.Tensor:
+             Q_dev: torch.Tensor, vol_dev: torch.Tensor, split_terms: int | None = None,
+             stream=None) -> torch.Tensor:
     """FDK from host projections to a host volume through caller-owned device buffers.
 
     E_host / vol_host should be pinned for asynchronous copies; the call returns

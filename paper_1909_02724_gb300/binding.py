@@ -24,7 +24,8 @@ IFDK_ERR_INVALID, IFDK_ERR_GEOMETRY, IFDK_ERR_ALIGNMENT, IFDK_ERR_CUDA = -1, -2,
 IFDK_ERR_TIMEOUT, IFDK_ERR_NOMEM, IFDK_ERR_UNSUPPORTED = -5, -6, -7
 
 # every symbol include/ifdk.h declares
-EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_adjoint", "ifdk_backproject",
+EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_size", "ifdk_filter_adjoint",
+           "ifdk_backproject",
            "ifdk_project", "ifdk_last_device_status", "ifdk_set_wait_limit", "ifdk_wait_selftest",
            "ifdk_backproject_info", "ifdk_query_backproject", "ifdk_status_string")
 
@@ -66,7 +67,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
         lib.ifdk_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_GeometryC)]
         lib.ifdk_destroy.argtypes = [vp]
-        lib.ifdk_filter.argtypes = [vp, vp, vp, i32, i32, vp]
+        lib.ifdk_filter.argtypes = [vp, vp, vp, i32, i32, vp, ctypes.c_size_t, vp]
+        lib.ifdk_filter_workspace_size.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_size_t),
+                                                   ctypes.POINTER(ctypes.c_size_t)]
         lib.ifdk_filter_adjoint.argtypes = [vp, vp, vp, vp]
         lib.ifdk_backproject.argtypes = [vp, vp, i32, i32, i32, vp, vp]
         lib.ifdk_project.argtypes = [vp, vp, vp, i32, i32, vp]
@@ -142,9 +145,17 @@ def ifdk_destroy(plan: int) -> None:
     _check(load_library().ifdk_destroy(plan), "ifdk_destroy")
 
 
-def ifdk_filter(plan: int, E, Q, q_dtype: int, split_terms: int = 0, stream=None) -> None:
-    _check(load_library().ifdk_filter(plan, _addr(E), _addr(Q), int(q_dtype), int(split_terms),
-                                      _stream(stream)), "ifdk_filter")
+def ifdk_filter(plan: int, E, Q, q_dtype: int, split_terms: int, workspace=None, workspace_bytes: int = 0,
+                stream=None) -> None:
+    _check(load_library().ifdk_filter(plan, _addr(E), _addr(Q), int(q_dtype), int(split_terms), _addr(workspace),
+                                      int(workspace_bytes), _stream(stream)), "ifdk_filter")
+
+
+def ifdk_filter_workspace_size(plan: int, split_terms: int) -> tuple[int, int]:
+    mn, pref = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load_library().ifdk_filter_workspace_size(plan, int(split_terms), ctypes.byref(mn), ctypes.byref(pref)),
+           "ifdk_filter_workspace_size")
+    return int(mn.value), int(pref.value)
 
 
 def ifdk_filter_adjoint(plan: int, G_Q, G_E, stream=None) -> None:
@@ -198,6 +209,7 @@ class Plan:
 
     def __init__(self, geom: Geometry):
         self.geom = geom
+        self._ws = {}
         self.handle = ifdk_create(geom)
 
     def close(self) -> None:
@@ -223,7 +235,24 @@ class Plan:
                 or tuple(t.shape) != (g.nx, g.ny, g.nz)):
             raise ValueError(f"vol must be a contiguous float32 CUDA tensor of shape {(g.nx, g.ny, g.nz)}")
 
-    def filter(self, E, Q=None, dtype=None, split_terms: int = 0, stream=None):
+    def workspace(self, split_terms: int, device):
+        """Filter workspace (cached per plan and split count; caller-side allocation)."""
+        import torch
+        if split_terms == 0:
+            return None, 0
+        key = (split_terms, str(device))
+        ws = self._ws.get(key)
+        if ws is None:
+            _, pref = ifdk_filter_workspace_size(self.handle, split_terms)
+            ws = torch.empty(pref // 2 + 64, dtype=torch.bfloat16, device=device)
+            self._ws[key] = ws
+        base = ws.data_ptr()
+        off = (-base) % 128
+        return base + off, ws.numel() * 2 - off
+
+    def filter(self, E, Q=None, dtype=None, split_terms: int | None = None, stream=None):
+        """Algorithm 1 on the tensor cores: split_terms defaults to 3 BF16 terms
+        for FP32 output and 2 for FP16 / BF16 output; 0 selects the SIMT kernel."""
         import torch
         self._check_views(E, "E")
         if E.dtype != torch.float32:
@@ -231,7 +260,10 @@ class Plan:
         if Q is None:
             Q = torch.empty_like(E, dtype=dtype or torch.float32)
         self._check_views(Q, "Q")
-        ifdk_filter(self.handle, E, Q, dtype_code(Q.dtype), split_terms, stream)
+        if split_terms is None:
+            split_terms = 3 if Q.dtype == torch.float32 else 2
+        ws, ws_bytes = self.workspace(split_terms, E.device)
+        ifdk_filter(self.handle, E, Q, dtype_code(Q.dtype), split_terms, ws, ws_bytes, stream)
         return Q
 
     def filter_adjoint(self, G_Q, out=None, stream=None):

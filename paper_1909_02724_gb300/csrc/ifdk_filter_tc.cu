@@ -1,0 +1,334 @@
+// Filtering stage (Algorithm 1 of the iFDK paper) on the 5th-generation
+// tensor cores: every detector row is multiplied by the Ram-Lak Toeplitz
+// matrix, Q = E~ . T with E~ = F_cos . E (rows = np * nv, K = N = nu) and
+// T[m][n] = h(n - m), which is symmetric because h is even.  That is the
+// exact linear convolution of Algorithm 1 as a dense GEMM.
+//
+// Precision: BF16 operands lose the cancellation the ramp filter relies on,
+// so both operands are split into s BF16 terms (x = x_0 + x_1 + x_2, each the
+// rounded remainder of the previous) and the products with i + j < s are
+// accumulated in FP32 in tensor memory: s = 3 keeps FP32-level accuracy,
+// s = 2 suits 16-bit storage, s = 1 is the plain BF16 product.
+//
+// Kernels: a pre-pass writes the cosine-weighted rows as s BF16 planes into
+// a caller-provided workspace (chunks of rows); the GEMM kernel computes one
+// 128 x 128 output tile per block: one lane streams A / B tiles by TMA
+// (128-byte swizzle) through a 4-stage mbarrier ring, one lane issues
+// tcgen05.mma (M = 128, N = 128, K = 16) into a TMEM accumulator, and the
+// four warps read it back (tcgen05.ld) and store the storage type.
+#include <cstring>
+
+#include "ifdk_device.cuh"
+#include "ifdk_internal.h"
+
+namespace ifdk {
+namespace {
+
+constexpr int kTcM = 128, kTcN = 128, kTcK = 64;
+constexpr int kTcStages = 4;
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTileA = kTcM * kTcK * 2, kTileB = kTcN * kTcK * 2;   // 16 KiB each
+constexpr uint32_t kTcSmemBars = kTcStages * (kTileA + kTileB);          // after the tiles
+constexpr size_t kTcSmem = 1024 + kTcSmemBars + 256;
+constexpr uint32_t kTmemCols = kTcN;                                      // FP32 accumulator columns
+
+struct TcArgs {
+    void *Q;
+    unsigned int *status;
+    unsigned long long wait_ns;
+    long long row0;       // first output row of this chunk
+    int nrows;            // rows in this chunk
+    int nu, nk, npairs;   // K blocks of 64, term pairs
+};
+
+// Term pairs (i, j), i + j < s, ordered by i + j: s = 1, 2, 3 use the first 1, 3, 6.
+__device__ __forceinline__ void term_pair(int q, int &i, int &j)
+{
+    i = (q == 2 || q == 4) ? 1 : (q == 5 ? 2 : 0);
+    j = (q == 1 || q == 4) ? 1 : (q == 3 ? 2 : 0);
+}
+
+template <typename TQ> __device__ __forceinline__ void store_row32(TQ *dst, const uint32_t (&r)[32], int n);
+template <> __device__ __forceinline__ void store_row32<float>(float *dst, const uint32_t (&r)[32], int n)
+{
+    if (n == 32 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            reinterpret_cast<uint4 *>(dst)[q] = make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    } else {
+        for (int q = 0; q < n; ++q) dst[q] = __uint_as_float(r[q]);
+    }
+}
+template <typename T16>
+__device__ __forceinline__ void store_row32_16(T16 *dst, const uint32_t (&r)[32], int n)
+{
+    if (n == 32 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const T16 lo = Storage<T16>::from_float(__uint_as_float(r[8 * q + 2 * e]));
+                const T16 hi = Storage<T16>::from_float(__uint_as_float(r[8 * q + 2 * e + 1]));
+                w[e] = (uint32_t)(*reinterpret_cast<const uint16_t *>(&lo)) |
+                       ((uint32_t)(*reinterpret_cast<const uint16_t *>(&hi)) << 16);
+            }
+            reinterpret_cast<uint4 *>(dst)[q] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else {
+        for (int q = 0; q < n; ++q) dst[q] = Storage<T16>::from_float(__uint_as_float(r[q]));
+    }
+}
+template <> __device__ __forceinline__ void store_row32<__half>(__half *dst, const uint32_t (&r)[32], int n)
+{
+    store_row32_16(dst, r, n);
+}
+template <> __device__ __forceinline__ void store_row32<__nv_bfloat16>(__nv_bfloat16 *dst, const uint32_t (&r)[32],
+                                                                      int n)
+{
+    store_row32_16(dst, r, n);
+}
+
+template <typename TQ>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    filter_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const TcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    const uint32_t sbase = smem_addr(smem_dyn);
+    const uint32_t s0 = sbase + ((1024u - (sbase & 1023u)) & 1023u);   // 128-byte swizzle wants 1 KiB alignment
+    const uint32_t tilesA = s0, tilesB = s0 + kTcStages * kTileA;
+    const uint32_t full = s0 + kTcSmemBars, empty = full + 8 * kTcStages, accum = empty + 8 * kTcStages;
+    const uint32_t tslot = accum + 8, abort_flag = tslot + 4;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m_tile = blockIdx.x, n_tile = blockIdx.y;
+    const int units = a.nk * a.npairs;
+
+    if (tid == 0) {
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(full + 8 * s, 1);
+            mbar_init(empty + 8 * s, 1);
+        }
+        mbar_init(accum, 1);
+        asm volatile("st.shared.u32 [%0], %1;" ::"r"(abort_flag), "r"(0u) : "memory");
+        fence_barrier_init();
+    }
+    if (warp == 0) tc::alloc(tslot, kTmemCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    uint32_t tmem;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(tslot) : "memory");
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer: unit u = (K block, term pair) into stage u % S
+        for (int u = 0; u < units; ++u) {
+            const int s = u % kTcStages;
+            if (!mbar_wait_bounded(empty + 8 * s, ((u / kTcStages) & 1) ^ 1, a.wait_ns)) {
+                asm volatile("st.shared.u32 [%0], %1;" ::"r"(abort_flag), "r"(1u) : "memory");
+                break;
+            }
+            int ti, tj;
+            term_pair(u % a.npairs, ti, tj);
+            const int kb = u / a.npairs;
+            mbar_arrive_expect_tx(full + 8 * s, kTileA + kTileB);
+            tma_load_3d(tilesA + s * kTileA, &tmA, kb * kTcK, m_tile * kTcM, ti, full + 8 * s);
+            tma_load_3d(tilesB + s * kTileB, &tmB, kb * kTcK, n_tile * kTcN, tj, full + 8 * s);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: 4 x (M128 N128 K16) per unit, accumulating in TMEM
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, kTcN);
+        for (int u = 0; u < units; ++u) {
+            const int s = u % kTcStages;
+            if (!mbar_wait_bounded(full + 8 * s, (u / kTcStages) & 1, a.wait_ns)) {
+                asm volatile("st.shared.u32 [%0], %1;" ::"r"(abort_flag), "r"(1u) : "memory");
+                break;
+            }
+            tc::fence_after();
+            const uint64_t da = tc::desc_sw128(tilesA + s * kTileA), db = tc::desc_sw128(tilesB + s * kTileB);
+#pragma unroll
+            for (int kk = 0; kk < kTcK / 16; ++kk)   // +32 bytes along K = +2 in the address field
+                tc::mma_f16(tmem, da + 2 * kk, db + 2 * kk, idesc, (u > 0 || kk > 0) ? 1u : 0u);
+            tc::commit(empty + 8 * s);
+        }
+        tc::commit(accum);   // arrives when every MMA issued above has completed
+    }
+    __syncwarp();
+
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 (tile rows), 32 columns at a time
+    const bool ok = mbar_wait_bounded(accum, 0, a.wait_ns);
+    tc::fence_after();
+    uint32_t aborted;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(aborted) : "r"(abort_flag) : "memory");
+    const int lrow = m_tile * kTcM + warp * 32 + lane;
+    const long long grow = a.row0 + lrow;
+    TQ *Q = static_cast<TQ *>(a.Q);
+#pragma unroll 1
+    for (int cb = 0; cb < kTcN / 32; ++cb) {
+        uint32_t r[32];
+        tc::ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), r);
+        tc::wait_ld();
+        const int col = n_tile * kTcN + cb * 32;
+        const int n = min(32, a.nu - col);
+        if (ok && !aborted && lrow < a.nrows && n > 0) store_row32<TQ>(Q + grow * a.nu + col, r, n);
+    }
+    if (!ok || aborted) {
+        if (tid == 0) atomicOr(a.status, kStatusTimeout);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::dealloc(tmem, kTmemCols);
+}
+
+// Cosine weight + BF16 split of rows [row0, row0 + nrows) into planes
+// ws[t][r][k] (t < terms, k < kpad, zero beyond nu): x = sum_t plane_t + O(2^-24 x).
+__global__ void __launch_bounds__(256)
+    filter_split_kernel(const float *__restrict__ E, const float *__restrict__ fcos, __nv_bfloat16 *ws, int nu,
+                        int nv, int kpad, long long row0, int nrows, int terms, long long plane)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int groups = kpad / 8;
+    const long long r = idx / groups;
+    const int k0 = (int)(idx - r * groups) * 8;
+    if (r >= nrows) return;
+    const long long grow = row0 + r;
+    const int v = (int)(grow % nv);
+    uint32_t w[3][4];
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+        float x[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int k = k0 + q + e;
+            x[e] = k < nu ? __ldg(E + grow * nu + k) * __ldg(fcos + (size_t)v * nu + k) : 0.0f;
+        }
+        uint16_t h[3][2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            float rem = x[e];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const __nv_bfloat16 b = __float2bfloat16_rn(rem);
+                rem -= __bfloat162float(b);
+                h[t][e] = *reinterpret_cast<const uint16_t *>(&b);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t) w[t][q / 2] = (uint32_t)h[t][0] | ((uint32_t)h[t][1] << 16);
+    }
+    for (int t = 0; t < terms; ++t)
+        *reinterpret_cast<uint4 *>(ws + t * plane + r * kpad + k0) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+}
+
+uint16_t f2bf(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);   // round to nearest even (finite inputs)
+    return (uint16_t)(u >> 16);
+}
+double bf2d(uint16_t b)
+{
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+int encode_bf16_3d(CUtensorMap *m, const void *base, uint64_t kpad, uint64_t rows, uint64_t planes, uint32_t box_rows)
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return IFDK_ERR_CUDA;
+    const cuuint64_t dims[3] = {kpad, rows, planes};
+    const cuuint64_t strides[2] = {kpad * 2, kpad * rows * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kTcK, box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS
+               ? IFDK_OK
+               : IFDK_ERR_CUDA;
+}
+
+template <typename TQ>
+int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size_t ws_bytes, cudaStream_t stream)
+{
+    const ifdk_geometry &g = p->g;
+    const int kpad = p->tc_kpad, npad = p->tc_npad;
+    const long long rows = (long long)g.np * g.nv;
+    const size_t row_bytes = (size_t)terms * kpad * 2;
+    long long cap = (long long)(ws_bytes / row_bytes) / kTcM * kTcM;
+    if (cap < kTcM) return IFDK_ERR_INVALID;
+    if (cap > rows) cap = (rows + kTcM - 1) / kTcM * kTcM;
+    if (cap > 65535LL * kTcM) cap = 65535LL * kTcM;
+    CUtensorMap tmA;
+    int rc = encode_bf16_3d(&tmA, ws, kpad, (uint64_t)cap, terms, kTcM);
+    if (rc != IFDK_OK) return rc;
+    auto kern = filter_tc_kernel<TQ>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) != cudaSuccess)
+        return IFDK_ERR_CUDA;
+    TcArgs a;
+    a.Q = Q;
+    a.status = p->d_status;
+    a.wait_ns = p->wait_ns;
+    a.nu = g.nu;
+    a.nk = kpad / kTcK;
+    a.npairs = terms * (terms + 1) / 2;
+    for (long long r0 = 0; r0 < rows; r0 += cap) {
+        const int nr = (int)(rows - r0 < cap ? rows - r0 : cap);
+        const long long threads = (long long)nr * (kpad / 8);
+        filter_split_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(
+            E, p->d_fcos, static_cast<__nv_bfloat16 *>(ws), g.nu, g.nv, kpad, r0, nr, terms, cap * kpad);
+        a.row0 = r0;
+        a.nrows = nr;
+        kern<<<dim3((nr + kTcM - 1) / kTcM, npad / kTcN), kTcThreads, kTcSmem, stream>>>(tmA, p->tc_tmap_b, a);
+        if (cudaGetLastError() != cudaSuccess) return IFDK_ERR_CUDA;
+    }
+    return IFDK_OK;
+}
+
+}  // namespace
+
+// Plan-time part: the Toeplitz matrix T[n][k] = h(n - k) as three BF16 planes
+// (FP64 taps split term by term), zero outside nu x nu.
+int plan_filter_tc(ifdk_plan_s *p)
+{
+    const int nu = p->g.nu;
+    p->tc_kpad = (nu + kTcK - 1) / kTcK * kTcK;
+    p->tc_npad = (nu + kTcN - 1) / kTcN * kTcN;
+    const size_t plane = (size_t)p->tc_npad * p->tc_kpad;
+    std::vector<uint16_t> t(3 * plane, 0);
+    for (int n = 0; n < nu; ++n)
+        for (int k = 0; k < nu; ++k) {
+            const int m = n - k;
+            const double h = m == 0 ? 0.25 : ((m & 1) ? -1.0 / (M_PI * M_PI * (double)m * m) : 0.0);
+            double rem = h;
+            for (int q = 0; q < 3; ++q) {
+                const uint16_t b = f2bf((float)rem);
+                t[q * plane + (size_t)n * p->tc_kpad + k] = b;
+                rem -= bf2d(b);
+            }
+        }
+    if (cudaMalloc(&p->d_tsplit, t.size() * 2) != cudaSuccess) return IFDK_ERR_NOMEM;
+    if (cudaMemcpy(p->d_tsplit, t.data(), t.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return IFDK_ERR_CUDA;
+    return encode_bf16_3d(&p->tc_tmap_b, p->d_tsplit, p->tc_kpad, p->tc_npad, 3, kTcN);
+}
+
+size_t filter_workspace_min(const ifdk_plan_s *p, int terms)
+{
+    return (size_t)terms * kTcM * p->tc_kpad * 2;
+}
+
+int launch_filter_tc(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int terms, void *ws, size_t ws_bytes,
+                     cudaStream_t stream)
+{
+    switch (q_dtype) {
+    case IFDK_F32: return launch_tc<float>(p, E, Q, terms, ws, ws_bytes, stream);
+    case IFDK_F16: return launch_tc<__half>(p, E, Q, terms, ws, ws_bytes, stream);
+    default: return launch_tc<__nv_bfloat16>(p, E, Q, terms, ws, ws_bytes, stream);
+    }
+}
+
+}  // namespace ifdk

@@ -69,6 +69,10 @@ struct ifdk_plan_s {
     bool fold_ok = false;                // mirror-pair fold path applicable
     ifdk::BpLaunch bp[3];                // per storage type
     unsigned long long wait_ns = 2000000000ull;
+    // tensor-core filter: Toeplitz matrix as 3 BF16 planes [3][tc_npad][tc_kpad]
+    int tc_kpad = 0, tc_npad = 0;
+    uint16_t *d_tsplit = nullptr;
+    CUtensorMap tc_tmap_b;
 };
 
 // Implemented in ifdk_bp.cu / ifdk_filter.cu / ifdk_project.cu.
@@ -78,6 +82,10 @@ int launch_backproject(ifdk_plan_s *p, const void *Q, int q_dtype, int view_begi
                        float *vol, cudaStream_t stream);
 int launch_filter(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int split_terms, bool adjoint,
                   cudaStream_t stream);
+int plan_filter_tc(ifdk_plan_s *p);
+size_t filter_workspace_min(const ifdk_plan_s *p, int terms);
+int launch_filter_tc(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int terms, void *ws, size_t ws_bytes,
+                     cudaStream_t stream);
 int launch_project(ifdk_plan_s *p, const float *vol, float *P, int view_begin, int view_count,
                    cudaStream_t stream);
 int launch_wait_selftest(ifdk_plan_s *p, unsigned long long ns, cudaStream_t stream);

@@ -167,6 +167,8 @@ int ifdk_create(ifdk_plan *out, const ifdk_geometry *gin)
          cudaMemset(p->d_status, 0, sizeof(unsigned int)) == cudaSuccess;
     if (!ok) { cudaGetLastError(); ifdk_destroy(p); return IFDK_ERR_CUDA; }
 
+    rc = plan_filter_tc(p);
+    if (rc != IFDK_OK) { cudaGetLastError(); ifdk_destroy(p); return rc; }
     plan_backproject(p);
     *out = p;
     return IFDK_OK;
@@ -182,17 +184,35 @@ int ifdk_destroy(ifdk_plan p)
     cudaFree(p->d_fcos);
     cudaFree(p->d_taps);
     cudaFree(p->d_status);
+    cudaFree(p->d_tsplit);
     if (dev >= 0 && dev != p->device) cudaSetDevice(dev);
     delete p;
     return IFDK_OK;
 }
 
-int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms, void *stream)
+int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms, void *workspace,
+                size_t workspace_bytes, void *stream)
 {
     if (!p || !E || !Q) return IFDK_ERR_INVALID;
     if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
     if (split_terms < 0 || split_terms > 3) return IFDK_ERR_INVALID;
-    return launch_filter(p, E, Q, q_dtype, split_terms, false, (cudaStream_t)stream);
+    if (split_terms == 0) return launch_filter(p, E, Q, q_dtype, 0, false, (cudaStream_t)stream);
+    if (!workspace || workspace_bytes < filter_workspace_min(p, split_terms)) return IFDK_ERR_INVALID;
+    if (((uintptr_t)workspace & 127) || ((uintptr_t)E & 15) || ((uintptr_t)Q & 15)) return IFDK_ERR_ALIGNMENT;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return IFDK_ERR_CUDA;
+    return launch_filter_tc(p, E, Q, q_dtype, split_terms, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int ifdk_filter_workspace_size(ifdk_plan p, int split_terms, size_t *min_bytes, size_t *preferred_bytes)
+{
+    if (!p || split_terms < 0 || split_terms > 3) return IFDK_ERR_INVALID;
+    const size_t mn = split_terms ? filter_workspace_min(p, split_terms) : 0;
+    const long long rows = (long long)p->g.np * p->g.nv;
+    const long long pref_rows = rows < 16384 ? (rows + 127) / 128 * 128 : 16384;
+    if (min_bytes) *min_bytes = mn;
+    if (preferred_bytes) *preferred_bytes = split_terms ? mn / 128 * (size_t)pref_rows : 0;
+    return IFDK_OK;
 }
 
 int ifdk_filter_adjoint(ifdk_plan p, const float *G_Q, float *G_E, void *stream)
