@@ -115,6 +115,31 @@ int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_ter
 int ifdk_filter_workspace_size(ifdk_plan p, int split_terms, size_t *min_bytes,
                                size_t *preferred_bytes);
 
+/* ifdk_filter's tensor-core path for callers that cannot allocate device
+   memory: the same computation and arguments as ifdk_filter with
+   split_terms 1..3, but the split-operand workspace is a fixed 16 MiB device
+   array inside the library instead of a caller buffer, and the call allocates
+   nothing.  It serves callers that own no device allocator at all (a plain C
+   program that only holds the E and Q buffers handed to it by a host
+   application) and callers that must not allocate once they run, such as
+   scanner pipelines that reserve all device memory at start-up and keep it
+   fixed while reconstructing.  The iFDK paper has no counterpart to this
+   call.
+   Limit: the array must hold one 128-row tile of split operands,
+   split_terms * 128 * ceil(nu / 64) * 64 * 2 bytes; larger requests return
+   IFDK_ERR_UNSUPPORTED before any work (nu up to 21845 for 3 terms).  Rows are
+   processed in launches of at most 16 MiB of operands, so it is slower than
+   ifdk_filter with a large workspace.
+   Every GPU that loads the library holds the 16 MiB until the process exits.
+   The first call on a device looks up the array's device address (with that
+   device current) and should come before any stream capture.  All calls share
+   the array and it keeps the previous call's contents (nothing in it has to
+   start at zero: every row read is written first by the same call); calls
+   whose work overlaps on the GPU (other streams, other host threads) race on
+   it and must be serialised by the caller. */
+int ifdk_filter_noalloc(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms,
+                        void *stream);
+
 /* Adjoint of ifdk_filter for FP32 (the Toeplitz matrix is symmetric because h
    is even, and F_cos is diagonal): G_E[s][v][m] = F_cos[v][m] sum_n h(n-m) G_Q[s][v][n].
    G_Q, G_E: device FP32 [np][nv][nu]; G_E is overwritten. */

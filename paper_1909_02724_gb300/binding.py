@@ -24,7 +24,8 @@ IFDK_ERR_INVALID, IFDK_ERR_GEOMETRY, IFDK_ERR_ALIGNMENT, IFDK_ERR_CUDA = -1, -2,
 IFDK_ERR_TIMEOUT, IFDK_ERR_NOMEM, IFDK_ERR_UNSUPPORTED = -5, -6, -7
 
 # every symbol include/ifdk.h declares
-EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_size", "ifdk_filter_adjoint",
+EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_size", "ifdk_filter_noalloc",
+           "ifdk_filter_adjoint",
            "ifdk_backproject",
            "ifdk_project", "ifdk_last_device_status", "ifdk_set_wait_limit", "ifdk_wait_selftest",
            "ifdk_backproject_info", "ifdk_query_backproject", "ifdk_status_string")
@@ -70,6 +71,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.ifdk_filter.argtypes = [vp, vp, vp, i32, i32, vp, ctypes.c_size_t, vp]
         lib.ifdk_filter_workspace_size.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_size_t),
                                                    ctypes.POINTER(ctypes.c_size_t)]
+        lib.ifdk_filter_noalloc.argtypes = [vp, vp, vp, i32, i32, vp]
         lib.ifdk_filter_adjoint.argtypes = [vp, vp, vp, vp]
         lib.ifdk_backproject.argtypes = [vp, vp, i32, i32, i32, vp, vp]
         lib.ifdk_project.argtypes = [vp, vp, vp, i32, i32, vp]
@@ -156,6 +158,12 @@ def ifdk_filter_workspace_size(plan: int, split_terms: int) -> tuple[int, int]:
     _check(load_library().ifdk_filter_workspace_size(plan, int(split_terms), ctypes.byref(mn), ctypes.byref(pref)),
            "ifdk_filter_workspace_size")
     return int(mn.value), int(pref.value)
+
+
+def ifdk_filter_noalloc(plan: int, E, Q, q_dtype: int, split_terms: int, stream=None) -> None:
+    """ifdk_filter's tensor-core path with the library's fixed 16 MiB workspace (allocates nothing)."""
+    _check(load_library().ifdk_filter_noalloc(plan, _addr(E), _addr(Q), int(q_dtype), int(split_terms),
+                                              _stream(stream)), "ifdk_filter_noalloc")
 
 
 def ifdk_filter_adjoint(plan: int, G_Q, G_E, stream=None) -> None:
