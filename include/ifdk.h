@@ -99,9 +99,11 @@ int ifdk_destroy(ifdk_plan p);
    E: device FP32 [np][nv][nu], read only, 16-byte aligned.  Q: device
    [np][nv][nu] of q_dtype (IFDK_F32, IFDK_F16 or IFDK_BF16), overwritten,
    16-byte aligned.  E and Q must not overlap.
-   split_terms = 1..3: tensor cores (tcgen05, BF16 operands each split into
-   that many terms, FP32 accumulation); 3 keeps FP32 accuracy, 2 suits 16-bit
-   storage.  It needs a device workspace of at least the minimum that
+   split_terms = 1..3: tensor cores (tcgen05, BF16 operands split into terms,
+   FP32 accumulation): 1 = one BF16 product; 2 = 2 terms each, 3 products,
+   for 16-bit storage; 3 = the weighted row as a double-float split into 4
+   terms and the taps into 3, 7 products, FP32-level accuracy even where the
+   ramp filter's cancellation amplifies FP32 input rounding (2048 pixels).  It needs a device workspace of at least the minimum that
    ifdk_filter_workspace_size reports, 128-byte aligned, owned by the caller
    and not used by anything else until the call's work has run (larger
    workspaces process more rows per launch).  split_terms = 0: FP32 SIMT
@@ -126,8 +128,9 @@ int ifdk_filter_workspace_size(ifdk_plan p, int split_terms, size_t *min_bytes,
    fixed while reconstructing.  The iFDK paper has no counterpart to this
    call.
    Limit: the array must hold one 128-row tile of split operands,
-   split_terms * 128 * ceil(nu / 64) * 64 * 2 bytes; larger requests return
-   IFDK_ERR_UNSUPPORTED before any work (nu up to 21845 for 3 terms).  Rows are
+   planes * 128 * ceil(nu / 64) * 64 * 2 bytes (planes = 1, 2, 4 for
+   split_terms 1, 2, 3); larger requests return IFDK_ERR_UNSUPPORTED before
+   any work (nu up to 16384 for 3 terms).  Rows are
    processed in launches of at most 16 MiB of operands, so it is slower than
    ifdk_filter with a large workspace.
    Every GPU that loads the library holds the 16 MiB until the process exits.

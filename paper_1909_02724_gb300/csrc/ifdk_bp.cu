@@ -20,7 +20,8 @@
 //   floats, so lanes on adjacent rows do not share banks).  FP16 / BF16
 //   storage first folds the two boxes into one array whose 8-byte element
 //   (m, c) holds Q[m][c], Q[2vc-m][c], Q[m][c+1], Q[2vc-m][c+1], so one load
-//   serves both voxels of a pair.
+//   serves both voxels of a pair.  FP16 taps are u-interpolated in FP16
+//   (packed half2) and widened once; BF16 taps are widened (a shift) first.
 // General kernel: any geometry (off-centre volume, fractional 2 v_c, large
 //   footprints, unaligned rows): Algorithm 4 without the mirror, taps read
 //   through the read-only cache with explicit bounds (zero outside).
@@ -277,41 +278,40 @@ __device__ __forceinline__ void write_run(const BpArgs &a, const Block &b, const
 template <typename T> struct FoldElem;
 template <> struct FoldElem<float> {
     static constexpr int ES = 16;
-    __device__ __forceinline__ static void load(uint32_t a, float2 &x, float2 &y)
+    // u-interpolated (direct, mirror) taps of one fold row
+    __device__ __forceinline__ static float2 row(uint32_t a, float2 du2, __half2)
     {
         const float4 e = lds_f32x4(a);
-        x = make_float2(e.x, e.y);
-        y = make_float2(e.z, e.w);
+        return lerp2(make_float2(e.x, e.y), make_float2(e.z, e.w), du2);
     }
 };
 template <> struct FoldElem<__half> {
     static constexpr int ES = 8;
-    __device__ __forceinline__ static void load(uint32_t a, float2 &x, float2 &y)
+    // the two stored FP16 taps are interpolated in FP16 (one packed sub + fma),
+    // and the result is widened to FP32 once
+    __device__ __forceinline__ static float2 row(uint32_t a, float2, __half2 duh)
     {
         const uint2 e = lds_u32x2(a);
         __half2 hx, hy;
         *reinterpret_cast<uint32_t *>(&hx) = e.x;
         *reinterpret_cast<uint32_t *>(&hy) = e.y;
-        x = __half22float2(hx);
-        y = __half22float2(hy);
+        return __half22float2(__hfma2(duh, __hsub2(hy, hx), hx));
     }
 };
 template <> struct FoldElem<__nv_bfloat16> {
     static constexpr int ES = 8;
-    __device__ __forceinline__ static void load(uint32_t a, float2 &x, float2 &y)
+    __device__ __forceinline__ static float2 row(uint32_t a, float2 du2, __half2)
     {
         const uint2 e = lds_u32x2(a);
-        x = make_float2(__uint_as_float(e.x << 16), __uint_as_float(e.x & 0xffff0000u));
-        y = make_float2(__uint_as_float(e.y << 16), __uint_as_float(e.y & 0xffff0000u));
+        return lerp2(make_float2(__uint_as_float(e.x << 16), __uint_as_float(e.x & 0xffff0000u)),
+                     make_float2(__uint_as_float(e.y << 16), __uint_as_float(e.y & 0xffff0000u)), du2);
     }
 };
 
 template <typename T>
-__device__ __forceinline__ float2 fold_row(uint32_t a, float2 du2)
+__device__ __forceinline__ float2 fold_row(uint32_t a, float2 du2, __half2 duh)
 {
-    float2 x, y;
-    FoldElem<T>::load(a, x, y);
-    return lerp2(x, y, du2);
+    return FoldElem<T>::row(a, du2, duh);
 }
 
 // The z-run of one (column, view): pair p samples rows n_p, n_p + 1 at
@@ -320,13 +320,14 @@ __device__ __forceinline__ float2 fold_row(uint32_t a, float2 du2)
 // and takes row n_p from the previous pair's upper row when it moved up;
 // otherwise both rows are loaded.  Both forms are branch-free.
 template <typename T, int ES, uint32_t ROW, bool REUSE>
-__device__ __forceinline__ void pair_loop(float2 *acc, uint32_t base, float sig, float vb, float2 du2, float2 W2)
+__device__ __forceinline__ void pair_loop(float2 *acc, uint32_t base, float sig, float vb, float2 du2, __half2 duh,
+                                          float2 W2)
 {
     constexpr int L = kPairs;
     float dv;
     uint32_t tv = floor_frac(vb, dv);
     uint32_t ad = base + tv * ROW;
-    float2 lo = fold_row<T>(ad, du2), hi = fold_row<T>(ad + ROW, du2);
+    float2 lo = fold_row<T>(ad, du2, duh), hi = fold_row<T>(ad + ROW, du2, duh);
     acc[0] = __ffma2_rn(W2, lerp2(lo, hi, make_float2(dv, dv)), acc[0]);
 #pragma unroll
     for (int p = 1; p < L; ++p) {
@@ -335,12 +336,12 @@ __device__ __forceinline__ void pair_loop(float2 *acc, uint32_t base, float sig,
         if constexpr (REUSE) {
             const bool moved = tn != tv;
             tv = tn;
-            const float2 hn = fold_row<T>(ad + ROW, du2);
+            const float2 hn = fold_row<T>(ad + ROW, du2, duh);
             lo = moved ? hi : lo;
             hi = hn;
         } else {
-            lo = fold_row<T>(ad, du2);
-            hi = fold_row<T>(ad + ROW, du2);
+            lo = fold_row<T>(ad, du2, duh);
+            hi = fold_row<T>(ad + ROW, du2, duh);
         }
         acc[p] = __ffma2_rn(W2, lerp2(lo, hi, make_float2(dv, dv)), acc[p]);
     }
@@ -426,11 +427,12 @@ __global__ void __launch_bounds__(kThreads, 3)
             // element (n, cu) = base + bits(t_v) * ROW, n = bits(t_v) - bias
             const uint32_t base = fbuf + (uint32_t)v * H * ROW + (cv.tu - kFloorBias) * ES - kFloorBias * ROW;
             const float2 du2 = make_float2(cv.du, cv.du), W2 = make_float2(cv.W, cv.W);
+            const __half2 duh = __float2half2_rn(cv.du);
             // sig < 1 - 2^-10 keeps fp32 rounding of v_{p+1} - v_p below one row
             if (__all_sync(0xffffffffu, cv.sig < 0.9990234375f))
-                pair_loop<T, ES, ROW, true>(acc, base, cv.sig, cv.vb, du2, W2);
+                pair_loop<T, ES, ROW, true>(acc, base, cv.sig, cv.vb, du2, duh, W2);
             else
-                pair_loop<T, ES, ROW, false>(acc, base, cv.sig, cv.vb, du2, W2);
+                pair_loop<T, ES, ROW, false>(acc, base, cv.sig, cv.vb, du2, duh, W2);
         }
         if (c + 1 < nchunks) fold_chunk(c + 1);
         __syncthreads();

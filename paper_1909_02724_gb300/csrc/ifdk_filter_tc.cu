@@ -4,11 +4,17 @@
 // T[m][n] = h(n - m), which is symmetric because h is even.  That is the
 // exact linear convolution of Algorithm 1 as a dense GEMM.
 //
-// Precision: BF16 operands lose the cancellation the ramp filter relies on,
-// so both operands are split into s BF16 terms (x = x_0 + x_1 + x_2, each the
-// rounded remainder of the previous) and the products with i + j < s are
-// accumulated in FP32 in tensor memory: s = 3 keeps FP32-level accuracy,
-// s = 2 suits 16-bit storage, s = 1 is the plain BF16 product.
+// Precision: the ramp filter removes the large smooth part of each row, so
+// the output is ~|w| / 1400 at 2048 pixels and input rounding is amplified by
+// that factor (rounding the weighted row w = F_cos E to FP32 alone costs
+// 1.3e-5 relative in Q).  Both operands are therefore split into BF16 terms
+// (each the rounded remainder of the previous) and the products of data term
+// i and tap term j are accumulated in FP32 in tensor memory:
+//   s = 1: (0,0);  s = 2: i + j <= 1;  s = 3: i + j <= 2 plus (3,0), with w
+//   formed as a double-float (FMA two-product of E and the hi/lo F_cos table)
+//   and split into 4 terms (~32 bits), the taps into 3 (24 bits).
+// s = 3 keeps the FDK result within FP32 tolerances at 2048 pixels; s = 2
+// suits 16-bit storage.
 //
 // Kernels: a pre-pass writes the cosine-weighted rows as s BF16 planes into
 // a caller-provided workspace (chunks of rows); the GEMM kernel computes one
@@ -16,6 +22,10 @@
 // (128-byte swizzle) through a 4-stage mbarrier ring, one lane issues
 // tcgen05.mma (M = 128, N = 128, K = 16) into a TMEM accumulator, and the
 // four warps read it back (tcgen05.ld) and store the storage type.
+// Accuracy: the central Ram-Lak taps are large and the long tail nearly
+// cancels them, so the K blocks around a tile's columns accumulate in their
+// own TMEM accumulator (few roundings at the large magnitude) and the left and
+// right tails in two others; the epilogue adds (left + right) + centre.
 #include <cstring>
 
 #include "ifdk_device.cuh"
@@ -30,7 +40,15 @@ constexpr int kTcThreads = 128;
 constexpr uint32_t kTileA = kTcM * kTcK * 2, kTileB = kTcN * kTcK * 2;   // 16 KiB each
 constexpr uint32_t kTcSmemBars = kTcStages * (kTileA + kTileB);          // after the tiles
 constexpr size_t kTcSmem = 1024 + kTcSmemBars + 256;
-constexpr uint32_t kTmemCols = kTcN;                                      // FP32 accumulator columns
+constexpr uint32_t kTmemCols = 4 * kTcN;   // three FP32 accumulators of kTcN columns (power-of-two allocation)
+
+// Accumulator of K block kb for output tile n_tile: 1 = the K blocks around the
+// tile's columns (the large central taps), 0 = left of them, 2 = right of them.
+__device__ __forceinline__ int k_group(int kb, int n_tile)
+{
+    const int first = n_tile * (kTcN / kTcK) - 1, last = (n_tile + 1) * (kTcN / kTcK);
+    return kb < first ? 0 : (kb > last ? 2 : 1);
+}
 
 struct TcArgs {
     void *Q;
@@ -41,10 +59,10 @@ struct TcArgs {
     int nu, nk, npairs;   // K blocks of 64, term pairs
 };
 
-// Term pairs (i, j), i + j < s, ordered by i + j: s = 1, 2, 3 use the first 1, 3, 6.
+// Term pairs (data i, tap j): s = 1, 2, 3 use the first 1, 3, 7.
 __device__ __forceinline__ void term_pair(int q, int &i, int &j)
 {
-    i = (q == 2 || q == 4) ? 1 : (q == 5 ? 2 : 0);
+    i = (q == 2 || q == 4) ? 1 : (q == 5 ? 2 : (q == 6 ? 3 : 0));
     j = (q == 1 || q == 4) ? 1 : (q == 3 ? 2 : 0);
 }
 
@@ -99,7 +117,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t s0 = sbase + ((1024u - (sbase & 1023u)) & 1023u);   // 128-byte swizzle wants 1 KiB alignment
     const uint32_t tilesA = s0, tilesB = s0 + kTcStages * kTileA;
     const uint32_t full = s0 + kTcSmemBars, empty = full + 8 * kTcStages, accum = empty + 8 * kTcStages;
-    const uint32_t tslot = accum + 8, abort_flag = tslot + 4;
+    const uint32_t tslot = accum + 8, abort_flag = tslot + 4;   // abort_flag + 4: accumulators written
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m_tile = blockIdx.x, n_tile = blockIdx.y;
     const int units = a.nk * a.npairs;
@@ -123,7 +141,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(tslot) : "memory");
 
     if (warp == 0 && lane == 0) {
-        // TMA producer: unit u = (K block, term pair) into stage u % S
+        // TMA producer: unit u = (K block u / npairs, term pair) into stage u % S
         for (int u = 0; u < units; ++u) {
             const int s = u % kTcStages;
             if (!mbar_wait_bounded(empty + 8 * s, ((u / kTcStages) & 1) ^ 1, a.wait_ns)) {
@@ -138,8 +156,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tma_load_3d(tilesB + s * kTileB, &tmB, kb * kTcK, n_tile * kTcN, tj, full + 8 * s);
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: 4 x (M128 N128 K16) per unit, accumulating in TMEM
+        // MMA issuer: 4 x (M128 N128 K16) per unit into one of three TMEM
+        // accumulators: K blocks left of, around, and right of this tile's columns
         constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, kTcN);
+        uint32_t started = 0;   // bit g: accumulator g has been written
         for (int u = 0; u < units; ++u) {
             const int s = u % kTcStages;
             if (!mbar_wait_bounded(full + 8 * s, (u / kTcStages) & 1, a.wait_ns)) {
@@ -147,12 +167,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 break;
             }
             tc::fence_after();
+            const int grp = k_group(u / a.npairs, n_tile);
+            const uint32_t d = tmem + (uint32_t)grp * kTcN;
             const uint64_t da = tc::desc_sw128(tilesA + s * kTileA), db = tc::desc_sw128(tilesB + s * kTileB);
 #pragma unroll
-            for (int kk = 0; kk < kTcK / 16; ++kk)   // +32 bytes along K = +2 in the address field
-                tc::mma_f16(tmem, da + 2 * kk, db + 2 * kk, idesc, (u > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < kTcK / 16; ++kk) {   // +32 bytes along K = +2 in the address field
+                tc::mma_f16(d, da + 2 * kk, db + 2 * kk, idesc, (started >> grp) & 1u);
+                started |= 1u << grp;
+            }
             tc::commit(empty + 8 * s);
         }
+        asm volatile("st.shared.u32 [%0], %1;" ::"r"(abort_flag + 4), "r"(started) : "memory");
         tc::commit(accum);   // arrives when every MMA issued above has completed
     }
     __syncwarp();
@@ -162,14 +187,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::fence_after();
     uint32_t aborted;
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(aborted) : "r"(abort_flag) : "memory");
+    uint32_t started;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(started) : "r"(abort_flag + 4) : "memory");
     const int lrow = m_tile * kTcM + warp * 32 + lane;
     const long long grow = a.row0 + lrow;
     TQ *Q = static_cast<TQ *>(a.Q);
 #pragma unroll 1
     for (int cb = 0; cb < kTcN / 32; ++cb) {
-        uint32_t r[32];
-        tc::ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), r);
+        // (left + right) + centre: the small tails first, one rounding each
+        uint32_t r[32], t[32];
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32);
+        tc::ld_32x32b_x32(ta + kTcN, r);
         tc::wait_ld();
+        if (!(started & 2u))
+            for (int q = 0; q < 32; ++q) r[q] = 0u;
+        if (started & 1u) {
+            tc::ld_32x32b_x32(ta, t);
+            tc::wait_ld();
+            for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(t[q]));
+        }
+        if (started & 4u) {
+            tc::ld_32x32b_x32(ta + 2 * kTcN, t);
+            tc::wait_ld();
+            for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(t[q]));
+        }
         const int col = n_tile * kTcN + cb * 32;
         const int n = min(32, a.nu - col);
         if (ok && !aborted && lrow < a.nrows && n > 0) store_row32<TQ>(Q + grow * a.nu + col, r, n);
@@ -183,10 +224,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // Cosine weight + BF16 split of rows [row0, row0 + nrows) into planes
-// ws[t][r][k] (t < terms, k < kpad, zero beyond nu): x = sum_t plane_t + O(2^-24 x).
+// ws[t][r][k] (k < kpad, zero beyond nu).  planes = 1, 2: terms of the FP32
+// product E F_cos; planes = 4: w = E (F_hi + F_lo) as a double-float p + c
+// (p = E F_hi rounded, c = the exact rounding error of p plus E F_lo), p split
+// exactly into 3 terms and c rounded into the 4th.
 __global__ void __launch_bounds__(256)
-    filter_split_kernel(const float *__restrict__ E, const float *__restrict__ fcos, __nv_bfloat16 *ws, int nu,
-                        int nv, int kpad, long long row0, int nrows, int terms, long long plane)
+    filter_split_kernel(const float *__restrict__ E, const float *__restrict__ fcos, const float *__restrict__ fcos_lo,
+                        __nv_bfloat16 *ws, int nu, int nv, int kpad, long long row0, int nrows, int planes,
+                        long long plane)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int groups = kpad / 8;
@@ -195,30 +240,33 @@ __global__ void __launch_bounds__(256)
     if (r >= nrows) return;
     const long long grow = row0 + r;
     const int v = (int)(grow % nv);
-    uint32_t w[3][4];
+    uint32_t w[4][4];
 #pragma unroll
     for (int q = 0; q < 8; q += 2) {
-        float x[2];
+        uint16_t h[4][2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int k = k0 + q + e;
-            x[e] = k < nu ? __ldg(E + grow * nu + k) * __ldg(fcos + (size_t)v * nu + k) : 0.0f;
-        }
-        uint16_t h[3][2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            float rem = x[e];
+            float p = 0.0f, c = 0.0f;
+            if (k < nu) {
+                const float x = __ldg(E + grow * nu + k), fh = __ldg(fcos + (size_t)v * nu + k);
+                p = x * fh;
+                c = fmaf(x, __ldg(fcos_lo + (size_t)v * nu + k), fmaf(x, fh, -p));
+            }
+            float rem = p;
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
                 const __nv_bfloat16 b = __float2bfloat16_rn(rem);
                 rem -= __bfloat162float(b);
                 h[t][e] = *reinterpret_cast<const uint16_t *>(&b);
             }
+            const __nv_bfloat16 b3 = __float2bfloat16_rn(c);
+            h[3][e] = *reinterpret_cast<const uint16_t *>(&b3);
         }
 #pragma unroll
-        for (int t = 0; t < 3; ++t) w[t][q / 2] = (uint32_t)h[t][0] | ((uint32_t)h[t][1] << 16);
+        for (int t = 0; t < 4; ++t) w[t][q / 2] = (uint32_t)h[t][0] | ((uint32_t)h[t][1] << 16);
     }
-    for (int t = 0; t < terms; ++t)
+    for (int t = 0; t < planes; ++t)
         *reinterpret_cast<uint4 *>(ws + t * plane + r * kpad + k0) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
 }
 
@@ -252,19 +300,22 @@ int encode_bf16_3d(CUtensorMap *m, const void *base, uint64_t kpad, uint64_t row
                : IFDK_ERR_CUDA;
 }
 
+// Data planes of split s (3 terms use the 4-plane double-float form).
+int data_planes(int terms) { return terms == 3 ? 4 : terms; }
+
 template <typename TQ>
 int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size_t ws_bytes, cudaStream_t stream)
 {
     const ifdk_geometry &g = p->g;
-    const int kpad = p->tc_kpad, npad = p->tc_npad;
+    const int kpad = p->tc_kpad, npad = p->tc_npad, planes = data_planes(terms);
     const long long rows = (long long)g.np * g.nv;
-    const size_t row_bytes = (size_t)terms * kpad * 2;
+    const size_t row_bytes = (size_t)planes * kpad * 2;
     long long cap = (long long)(ws_bytes / row_bytes) / kTcM * kTcM;
     if (cap < kTcM) return IFDK_ERR_INVALID;
     if (cap > rows) cap = (rows + kTcM - 1) / kTcM * kTcM;
     if (cap > 65535LL * kTcM) cap = 65535LL * kTcM;
     CUtensorMap tmA;
-    int rc = encode_bf16_3d(&tmA, ws, kpad, (uint64_t)cap, terms, kTcM);
+    int rc = encode_bf16_3d(&tmA, ws, kpad, (uint64_t)cap, planes, kTcM);
     if (rc != IFDK_OK) return rc;
     auto kern = filter_tc_kernel<TQ>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) != cudaSuccess)
@@ -275,12 +326,13 @@ int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size
     a.wait_ns = p->wait_ns;
     a.nu = g.nu;
     a.nk = kpad / kTcK;
-    a.npairs = terms * (terms + 1) / 2;
+    a.npairs = terms == 3 ? 7 : (terms == 2 ? 3 : 1);
     for (long long r0 = 0; r0 < rows; r0 += cap) {
         const int nr = (int)(rows - r0 < cap ? rows - r0 : cap);
         const long long threads = (long long)nr * (kpad / 8);
         filter_split_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(
-            E, p->d_fcos, static_cast<__nv_bfloat16 *>(ws), g.nu, g.nv, kpad, r0, nr, terms, cap * kpad);
+            E, p->d_fcos, p->d_fcos_lo, static_cast<__nv_bfloat16 *>(ws), g.nu, g.nv, kpad, r0, nr, planes,
+            cap * kpad);
         a.row0 = r0;
         a.nrows = nr;
         kern<<<dim3((nr + kTcM - 1) / kTcM, npad / kTcN), kTcThreads, kTcSmem, stream>>>(tmA, p->tc_tmap_b, a);
@@ -318,7 +370,7 @@ int plan_filter_tc(ifdk_plan_s *p)
 
 size_t filter_workspace_min(const ifdk_plan_s *p, int terms)
 {
-    return (size_t)terms * kTcM * p->tc_kpad * 2;
+    return (size_t)data_planes(terms) * kTcM * p->tc_kpad * 2;
 }
 
 int launch_filter_tc(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int terms, void *ws, size_t ws_bytes,

@@ -62,6 +62,7 @@ struct ifdk_plan_s {
     int device = 0;
     ifdk::ViewTerms *d_terms = nullptr;  // [np]
     float *d_fcos = nullptr;             // [nv][nu]
+    float *d_fcos_lo = nullptr;          // [nv][nu], F_cos - (float)F_cos
     float *d_taps = nullptr;             // [2 nu - 1], index m + nu - 1
     unsigned int *d_status = nullptr;    // device status word
     double uc = 0, vc = 0;               // principal point (pixels)

@@ -144,11 +144,13 @@ int ifdk_create(ifdk_plan *out, const ifdk_geometry *gin)
     const ifdk_geometry &g = p->g;
 
     // Cosine weight D / sqrt(D^2 + a^2 + b^2) and Ram-Lak taps, FP64 then FP32.
-    std::vector<float> fcos((size_t)g.nu * g.nv), taps(2 * (size_t)g.nu - 1);
+    std::vector<float> fcos((size_t)g.nu * g.nv), fcos_lo(fcos.size()), taps(2 * (size_t)g.nu - 1);
     for (int iv = 0; iv < g.nv; ++iv)
         for (int iu = 0; iu < g.nu; ++iu) {
             const double a = (iu - p->uc) * g.du, b = (iv - p->vc) * g.dv;
-            fcos[(size_t)iv * g.nu + iu] = (float)(g.sdd / std::sqrt(g.sdd * g.sdd + a * a + b * b));
+            const double f = g.sdd / std::sqrt(g.sdd * g.sdd + a * a + b * b);
+            fcos[(size_t)iv * g.nu + iu] = (float)f;
+            fcos_lo[(size_t)iv * g.nu + iu] = (float)(f - (double)(float)f);
         }
     for (int m = -(g.nu - 1); m <= g.nu - 1; ++m) {
         const double h = m == 0 ? 0.25 : (m % 2 == 0 ? 0.0 : -1.0 / (M_PI * M_PI * (double)m * m));
@@ -158,11 +160,13 @@ int ifdk_create(ifdk_plan *out, const ifdk_geometry *gin)
     if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return IFDK_ERR_CUDA; }
     bool ok = cudaMalloc(&p->d_terms, sizeof(ViewTerms) * g.np) == cudaSuccess &&
               cudaMalloc(&p->d_fcos, sizeof(float) * fcos.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_fcos_lo, sizeof(float) * fcos.size()) == cudaSuccess &&
               cudaMalloc(&p->d_taps, sizeof(float) * taps.size()) == cudaSuccess &&
               cudaMalloc(&p->d_status, sizeof(unsigned int)) == cudaSuccess;
     if (!ok) { cudaGetLastError(); ifdk_destroy(p); return IFDK_ERR_NOMEM; }
     ok = cudaMemcpy(p->d_terms, p->terms.data(), sizeof(ViewTerms) * g.np, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(p->d_fcos, fcos.data(), sizeof(float) * fcos.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(p->d_fcos_lo, fcos_lo.data(), sizeof(float) * fcos.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(p->d_taps, taps.data(), sizeof(float) * taps.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemset(p->d_status, 0, sizeof(unsigned int)) == cudaSuccess;
     if (!ok) { cudaGetLastError(); ifdk_destroy(p); return IFDK_ERR_CUDA; }
@@ -182,6 +186,7 @@ int ifdk_destroy(ifdk_plan p)
     if (dev != p->device) cudaSetDevice(p->device);
     cudaFree(p->d_terms);
     cudaFree(p->d_fcos);
+    cudaFree(p->d_fcos_lo);
     cudaFree(p->d_taps);
     cudaFree(p->d_status);
     cudaFree(p->d_tsplit);
