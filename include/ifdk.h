@@ -99,15 +99,18 @@ int ifdk_destroy(ifdk_plan p);
    E: device FP32 [np][nv][nu], read only, 16-byte aligned.  Q: device
    [np][nv][nu] of q_dtype (IFDK_F32, IFDK_F16 or IFDK_BF16), overwritten,
    16-byte aligned.  E and Q must not overlap.
-   split_terms = 1..3: tensor cores (tcgen05, BF16 operands split into terms,
-   FP32 accumulation): 1 = one BF16 product; 2 = 2 terms each, 3 products,
-   for 16-bit storage; 3 = the weighted row as a double-float split into 4
-   terms and the taps into 3, 7 products, FP32-level accuracy even where the
-   ramp filter's cancellation amplifies FP32 input rounding (2048 pixels).  It needs a device workspace of at least the minimum that
+   split_terms = 1..3: tensor cores (tcgen05).  The convolution is summed by
+   parts, Q = sum_k g(n-k) d(k) over k = 0..nu, with d the first difference of
+   the weighted row and g the running sum of the taps (the same result, but
+   without the ~1400x cancellation of the direct sum at 2048 pixels); BF16
+   operands are split into terms and accumulated in FP32: 1 = one BF16
+   product; 2 = 2 terms each, 3 products, for 16-bit storage; 3 = 3 terms
+   each, 6 products, FP32-level accuracy.  It needs a device workspace of at
+   least the minimum that
    ifdk_filter_workspace_size reports, 128-byte aligned, owned by the caller
    and not used by anything else until the call's work has run (larger
    workspaces process more rows per launch).  split_terms = 0: FP32 SIMT
-   kernel, workspace ignored (may be NULL). */
+   kernel of the direct sum, workspace ignored (may be NULL). */
 int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms,
                 void *workspace, size_t workspace_bytes, void *stream);
 
@@ -128,9 +131,8 @@ int ifdk_filter_workspace_size(ifdk_plan p, int split_terms, size_t *min_bytes,
    fixed while reconstructing.  The iFDK paper has no counterpart to this
    call.
    Limit: the array must hold one 128-row tile of split operands,
-   planes * 128 * ceil(nu / 64) * 64 * 2 bytes (planes = 1, 2, 4 for
-   split_terms 1, 2, 3); larger requests return IFDK_ERR_UNSUPPORTED before
-   any work (nu up to 16384 for 3 terms).  Rows are
+   split_terms * 128 * ceil((nu + 1) / 64) * 64 * 2 bytes; larger requests
+   return IFDK_ERR_UNSUPPORTED before any work (nu up to 21823 for 3 terms).  Rows are
    processed in launches of at most 16 MiB of operands, so it is slower than
    ifdk_filter with a large workspace.
    Every GPU that loads the library holds the 16 MiB until the process exits.

@@ -1,14 +1,18 @@
 // Filtering stage (Algorithm 1 of the iFDK paper): cosine weight F_cos then
-// the Ram-Lak ramp convolution of every detector row, computed as the dense
-// Toeplitz product Q_row = T . (F_cos . E_row), T[n][m] = h(n - m), which is
-// the exact linear (zero padded) convolution truncated to Nu outputs.
+// the Ram-Lak ramp convolution of every detector row, the exact linear (zero
+// padded) convolution truncated to Nu outputs, as a dense Toeplitz product.
 //
-// FP32 SIMT kernel: a block computes 1024 consecutive outputs of kRows rows;
-// the weighted rows and the taps the block needs sit in shared memory; every
-// thread keeps 4 consecutive outputs x kRows rows in registers and slides a
-// 4-tap window down the Toeplitz diagonal.  The cosine weight is applied when
-// the rows are staged (or to the outputs, for the adjoint), and the epilogue
-// casts to the storage type.
+// FP32 SIMT kernel.  The forward filter sums by parts: with w = F_cos E (0
+// outside the row), d(m) = w(m) - w(m-1) for m in [0, nu] and the running tap
+// sum g(n) = sum_{j <= n} h(j), Q(n) = sum_m g(n - m) d(m), which avoids the
+// ~1400x cancellation of the direct sum at 2048 pixels (d is formed from a
+// double-float w).  The adjoint (gradient) is the direct transpose,
+// F_cos . (T^T q) with T[n][m] = h(n - m).
+//
+// A block computes 1024 consecutive outputs of kRows rows; the input rows
+// and the taps the block needs sit in shared memory; every thread keeps 4
+// consecutive outputs x kRows rows in registers and slides a 4-tap window
+// down the Toeplitz diagonal; the epilogue casts to the storage type.
 #include "ifdk_device.cuh"
 #include "ifdk_internal.h"
 
@@ -20,33 +24,61 @@ constexpr int kOutPerThread = 4;  // consecutive outputs per thread
 constexpr int kFThreads = 256;
 constexpr int kOutPerBlock = kFThreads * kOutPerThread;
 
+// Weighted sample w(m) = E F_cos as a double-float p + c; 0 outside [0, nu).
+__device__ __forceinline__ void weighted_df(const float *__restrict__ Erow, const float *__restrict__ fh_row,
+                                            const float *__restrict__ fl_row, int m, int nu, float &p, float &c)
+{
+    p = 0.0f;
+    c = 0.0f;
+    if (m >= 0 && m < nu) {
+        const float x = __ldg(Erow + m), fh = __ldg(fh_row + m);
+        p = x * fh;
+        c = fmaf(x, __ldg(fl_row + m), fmaf(x, fh, -p));
+    }
+}
+
+// Forward: len = nu + 1 inputs d(m), taps = g with tap(n) = taps[n + nu] for
+// n in [-nu, nu - 1].  Adjoint: len = nu inputs q(m), taps = h with
+// tap(n) = taps[n + nu - 1] for |n| < nu.
 template <typename TQ, bool ADJ>
 __global__ void __launch_bounds__(kFThreads)
     filter_simt_kernel(const float *__restrict__ E, TQ *__restrict__ Q, const float *__restrict__ fcos,
-                       const float *__restrict__ taps, int nu, int nv, long long rows)
+                       const float *__restrict__ fcos_lo, const float *__restrict__ taps, int nu, int nv,
+                       long long rows)
 {
     extern __shared__ float sm[];
-    float *w = sm;                        // [kRows][nu] weighted input rows
-    float *hs = sm + kRows * nu;          // taps window, see below
+    const int len = ADJ ? nu : nu + 1;
+    float *w = sm;                        // [kRows][len] input rows
+    float *hs = sm + kRows * len;         // taps window, see below
     const int n_lo = blockIdx.x * kOutPerBlock;
     const long long r0 = (long long)blockIdx.y * kRows;
 
     for (int r = 0; r < kRows; ++r) {
         const long long row = r0 + r;
-        for (int m = threadIdx.x; m < nu; m += kFThreads) {
+        for (int m = threadIdx.x; m < len; m += kFThreads) {
             float x = 0.0f;
             if (row < rows) {
-                x = __ldg(E + row * nu + m);
-                if (!ADJ) x *= __ldg(fcos + (row % nv) * nu + m);
+                if (ADJ) {
+                    x = __ldg(E + row * nu + m);
+                } else {
+                    const size_t vo = (size_t)(row % nv) * nu;
+                    float p1, c1, p0, c0;
+                    weighted_df(E + row * nu, fcos + vo, fcos_lo + vo, m, nu, p1, c1);
+                    weighted_df(E + row * nu, fcos + vo, fcos_lo + vo, m - 1, nu, p0, c0);
+                    const float s = p1 - p0, bb = s - p1;
+                    const float err = (p1 - (s - bb)) + (-p0 - bb);   // s + err = p1 - p0 exactly
+                    x = s + (err + (c1 - c0));
+                }
             }
-            w[r * nu + m] = x;
+            w[r * len + m] = x;
         }
     }
-    // hs[t] = h(d) with d = t - 4 + n_lo - (nu - 1), for d in the range the block uses.
-    const int hlen = kOutPerBlock + nu + 4;
+    // hs[t] = tap(n) with n = t - 4 + n_lo - (len - 1), for n in the range the block uses.
+    const int hlen = kOutPerBlock + len + 4;
     for (int t = threadIdx.x; t < hlen; t += kFThreads) {
-        const int d = t - 4 + n_lo - (nu - 1);
-        hs[t] = (d > -nu && d < nu) ? __ldg(taps + d + nu - 1) : 0.0f;
+        const int n = t - 4 + n_lo - (len - 1);
+        hs[t] = ADJ ? ((n > -nu && n < nu) ? __ldg(taps + n + nu - 1) : 0.0f)
+                    : ((n >= -nu && n < nu) ? __ldg(taps + n + nu) : 0.0f);
     }
     __syncthreads();
 
@@ -57,13 +89,13 @@ __global__ void __launch_bounds__(kFThreads)
     for (int r = 0; r < kRows; ++r)
 #pragma unroll
         for (int q = 0; q < kOutPerThread; ++q) acc[r][q] = 0.0f;
-    // output n0+q at input m uses h(n0 + q - m) = hs[base + q - m]
-    const int base = threadIdx.x * kOutPerThread + nu - 1 + 4;
+    // output n0+q at input m uses tap(n0 + q - m) = hs[base + q - m]
+    const int base = threadIdx.x * kOutPerThread + len - 1 + 4;
     float h0 = hs[base], h1 = hs[base + 1], h2 = hs[base + 2], h3 = hs[base + 3];
-    for (int m = 0; m < nu; ++m) {
+    for (int m = 0; m < len; ++m) {
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
-            const float x = w[r * nu + m];
+            const float x = w[r * len + m];
             acc[r][0] = fmaf(h0, x, acc[r][0]);
             acc[r][1] = fmaf(h1, x, acc[r][1]);
             acc[r][2] = fmaf(h2, x, acc[r][2]);
@@ -95,7 +127,8 @@ int launch_simt(ifdk_plan_s *p, const float *E, void *Q, cudaStream_t stream)
 {
     const ifdk_geometry &g = p->g;
     const long long rows = (long long)g.np * g.nv;
-    const size_t smem = sizeof(float) * ((size_t)kRows * g.nu + kOutPerBlock + g.nu + 4);
+    const int len = ADJ ? g.nu : g.nu + 1;
+    const size_t smem = sizeof(float) * ((size_t)kRows * len + kOutPerBlock + len + 4);
     if (smem > 220 * 1024) return IFDK_ERR_UNSUPPORTED;
     // grid.y is limited to 65535 blocks: launch whole views at a time so that
     // every launch starts on detector row 0 (the F_cos row is row % nv).
@@ -109,7 +142,8 @@ int launch_simt(ifdk_plan_s *p, const float *E, void *Q, cudaStream_t stream)
     for (long long r0 = 0; r0 < rows; r0 += chunk) {
         const long long nr = rows - r0 < chunk ? rows - r0 : chunk;
         kern<<<dim3(gx, (unsigned)((nr + kRows - 1) / kRows)), kFThreads, smem, stream>>>(
-            E + r0 * g.nu, static_cast<TQ *>(Q) + r0 * g.nu, p->d_fcos, p->d_taps, g.nu, g.nv, nr);
+            E + r0 * g.nu, static_cast<TQ *>(Q) + r0 * g.nu, p->d_fcos, p->d_fcos_lo, ADJ ? p->d_taps : p->d_gsum,
+            g.nu, g.nv, nr);
         if (cudaGetLastError() != cudaSuccess) return IFDK_ERR_CUDA;
     }
     return IFDK_OK;

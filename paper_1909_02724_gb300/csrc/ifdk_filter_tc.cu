@@ -1,31 +1,30 @@
 // Filtering stage (Algorithm 1 of the iFDK paper) on the 5th-generation
-// tensor cores: every detector row is multiplied by the Ram-Lak Toeplitz
-// matrix, Q = E~ . T with E~ = F_cos . E (rows = np * nv, K = N = nu) and
-// T[m][n] = h(n - m), which is symmetric because h is even.  That is the
-// exact linear convolution of Algorithm 1 as a dense GEMM.
+// tensor cores, as a dense Toeplitz GEMM over detector rows.
 //
-// Precision: the ramp filter removes the large smooth part of each row, so
-// the output is ~|w| / 1400 at 2048 pixels and input rounding is amplified by
-// that factor (rounding the weighted row w = F_cos E to FP32 alone costs
-// 1.3e-5 relative in Q).  Both operands are therefore split into BF16 terms
-// (each the rounded remainder of the previous) and the products of data term
-// i and tap term j are accumulated in FP32 in tensor memory:
-//   s = 1: (0,0);  s = 2: i + j <= 1;  s = 3: i + j <= 2 plus (3,0), with w
-//   formed as a double-float (FMA two-product of E and the hi/lo F_cos table)
-//   and split into 4 terms (~32 bits), the taps into 3 (24 bits).
-// s = 3 keeps the FDK result within FP32 tolerances at 2048 pixels; s = 2
-// suits 16-bit storage.
+// Summation by parts: with the weighted row w = F_cos E (w = 0 outside
+// [0, nu)), its first difference d(k) = w(k) - w(k-1) for k in [0, nu], and
+// the running sum of the Ram-Lak taps g(m) = sum_{j <= m} h(j)
+// (j from -(nu-1)), the exact linear convolution of Algorithm 1 is
+//     Q(u) = sum_k h(u - k) w(k) = sum_{k=0}^{nu} g(u - k) d(k).
+// The ramp filter removes the large smooth part of each row: at 2048 pixels
+// |w| is ~1400 x |Q|, so in the first form every rounding of w or of a
+// partial sum is amplified ~1400 times; d is ~6 x |Q| and g is bounded by
+// 1/8 (it decays like 1/(2 pi^2 m)), so the second form is well conditioned
+// and FP32 accumulation suffices.  The GEMM is Q = D . G with K = nu + 1.
 //
-// Kernels: a pre-pass writes the cosine-weighted rows as s BF16 planes into
-// a caller-provided workspace (chunks of rows); the GEMM kernel computes one
-// 128 x 128 output tile per block: one lane streams A / B tiles by TMA
-// (128-byte swizzle) through a 4-stage mbarrier ring, one lane issues
-// tcgen05.mma (M = 128, N = 128, K = 16) into a TMEM accumulator, and the
-// four warps read it back (tcgen05.ld) and store the storage type.
-// Accuracy: the central Ram-Lak taps are large and the long tail nearly
-// cancels them, so the K blocks around a tile's columns accumulate in their
-// own TMEM accumulator (few roundings at the large magnitude) and the left and
-// right tails in two others; the epilogue adds (left + right) + centre.
+// Both operands are split into BF16 terms (each the rounded remainder of the
+// previous) and the products of data term i and tap term j are accumulated in
+// FP32 in tensor memory: s = 1: (0,0); s = 2: i + j <= 1; s = 3: i + j <= 2
+// (FP32 d is exactly three BF16 terms, the taps get 24 bits).  d is formed
+// from w as a double-float (FMA two-product of E with the hi/lo F_cos table),
+// so that FP32 rounding of w is not differenced.
+//
+// Kernels: a pre-pass writes d of a chunk of rows as s BF16 planes into a
+// caller-provided workspace; the GEMM kernel computes one 128 x 128 output
+// tile per block: one lane streams A / B tiles by TMA (128-byte swizzle)
+// through a 4-stage mbarrier ring, one lane issues tcgen05.mma (M = 128,
+// N = 128, K = 16) into four TMEM accumulators (see acc_of), and the four
+// warps read them back (tcgen05.ld), add them and store the storage type.
 #include <cstring>
 
 #include "ifdk_device.cuh"
@@ -40,15 +39,16 @@ constexpr int kTcThreads = 128;
 constexpr uint32_t kTileA = kTcM * kTcK * 2, kTileB = kTcN * kTcK * 2;   // 16 KiB each
 constexpr uint32_t kTcSmemBars = kTcStages * (kTileA + kTileB);          // after the tiles
 constexpr size_t kTcSmem = 1024 + kTcSmemBars + 256;
-constexpr uint32_t kTmemCols = 4 * kTcN;   // three FP32 accumulators of kTcN columns (power-of-two allocation)
+constexpr int kAccs = 4;
+constexpr uint32_t kTmemCols = kAccs * kTcN;   // four FP32 accumulators of kTcN columns
 
-// Accumulator of K block kb for output tile n_tile: 1 = the K blocks around the
-// tile's columns (the large central taps), 0 = left of them, 2 = right of them.
-__device__ __forceinline__ int k_group(int kb, int n_tile)
-{
-    const int first = n_tile * (kTcN / kTcK) - 1, last = (n_tile + 1) * (kTcN / kTcK);
-    return kb < first ? 0 : (kb > last ? 2 : 1);
-}
+// TMEM accumulator of unit (K block kb, term pair q): the leading product
+// (q = 0) rotates over three accumulators by K block, the small cross
+// products share the fourth.  The tensor cores' accumulation into TMEM is
+// not round-to-nearest FP32, and its error grows with the number of MMAs
+// accumulated at a given magnitude; splitting the steps this way and adding
+// the four in FP32 in the epilogue keeps it ~20x below one accumulator's.
+__device__ __forceinline__ int acc_of(int kb, int q) { return q == 0 ? kb % 3 : 3; }
 
 struct TcArgs {
     void *Q;
@@ -59,10 +59,10 @@ struct TcArgs {
     int nu, nk, npairs;   // K blocks of 64, term pairs
 };
 
-// Term pairs (data i, tap j): s = 1, 2, 3 use the first 1, 3, 7.
+// Term pairs (data i, tap j): s = 1, 2, 3 use the first 1, 3, 6.
 __device__ __forceinline__ void term_pair(int q, int &i, int &j)
 {
-    i = (q == 2 || q == 4) ? 1 : (q == 5 ? 2 : (q == 6 ? 3 : 0));
+    i = (q == 2 || q == 4) ? 1 : (q == 5 ? 2 : 0);
     j = (q == 1 || q == 4) ? 1 : (q == 3 ? 2 : 0);
 }
 
@@ -156,10 +156,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tma_load_3d(tilesB + s * kTileB, &tmB, kb * kTcK, n_tile * kTcN, tj, full + 8 * s);
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: 4 x (M128 N128 K16) per unit into one of three TMEM
-        // accumulators: K blocks left of, around, and right of this tile's columns
+        // MMA issuer: 4 x (M128 N128 K16) per unit into TMEM accumulator acc_of(kb, q)
         constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, kTcN);
-        uint32_t started = 0;   // bit g: accumulator g has been written
+        uint32_t started = 0;   // bit c: accumulator c has been written
         for (int u = 0; u < units; ++u) {
             const int s = u % kTcStages;
             if (!mbar_wait_bounded(full + 8 * s, (u / kTcStages) & 1, a.wait_ns)) {
@@ -167,13 +166,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 break;
             }
             tc::fence_after();
-            const int grp = k_group(u / a.npairs, n_tile);
-            const uint32_t d = tmem + (uint32_t)grp * kTcN;
+            const int c = acc_of(u / a.npairs, u % a.npairs);
+            const uint32_t d = tmem + (uint32_t)c * kTcN;
             const uint64_t da = tc::desc_sw128(tilesA + s * kTileA), db = tc::desc_sw128(tilesB + s * kTileB);
 #pragma unroll
             for (int kk = 0; kk < kTcK / 16; ++kk) {   // +32 bytes along K = +2 in the address field
-                tc::mma_f16(d, da + 2 * kk, db + 2 * kk, idesc, (started >> grp) & 1u);
-                started |= 1u << grp;
+                tc::mma_f16(d, da + 2 * kk, db + 2 * kk, idesc, (started >> c) & 1u);
+                started |= 1u << c;
             }
             tc::commit(empty + 8 * s);
         }
@@ -194,21 +193,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     TQ *Q = static_cast<TQ *>(a.Q);
 #pragma unroll 1
     for (int cb = 0; cb < kTcN / 32; ++cb) {
-        // (left + right) + centre: the small tails first, one rounding each
+        // sum of the accumulators written, in FP32 (round to nearest)
         uint32_t r[32], t[32];
         const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32);
-        tc::ld_32x32b_x32(ta + kTcN, r);
-        tc::wait_ld();
-        if (!(started & 2u))
-            for (int q = 0; q < 32; ++q) r[q] = 0u;
-        if (started & 1u) {
-            tc::ld_32x32b_x32(ta, t);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) r[q] = 0u;
+#pragma unroll
+        for (int c = 0; c < kAccs; ++c) {
+            if (!((started >> c) & 1u)) continue;
+            tc::ld_32x32b_x32(ta + (uint32_t)c * kTcN, t);
             tc::wait_ld();
-            for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(t[q]));
-        }
-        if (started & 4u) {
-            tc::ld_32x32b_x32(ta + 2 * kTcN, t);
-            tc::wait_ld();
+#pragma unroll
             for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(t[q]));
         }
         const int col = n_tile * kTcN + cb * 32;
@@ -223,11 +218,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (warp == 0) tc::dealloc(tmem, kTmemCols);
 }
 
-// Cosine weight + BF16 split of rows [row0, row0 + nrows) into planes
-// ws[t][r][k] (k < kpad, zero beyond nu).  planes = 1, 2: terms of the FP32
-// product E F_cos; planes = 4: w = E (F_hi + F_lo) as a double-float p + c
-// (p = E F_hi rounded, c = the exact rounding error of p plus E F_lo), p split
-// exactly into 3 terms and c rounded into the 4th.
+// Weighted row w(k) = E F_cos as a double-float p + c (p = E F_hi rounded,
+// c = the exact rounding error of p plus E F_lo); 0 outside [0, nu).
+__device__ __forceinline__ void weighted(const float *__restrict__ Erow, const float *__restrict__ fh_row,
+                                         const float *__restrict__ fl_row, int k, int nu, float &p, float &c)
+{
+    p = 0.0f;
+    c = 0.0f;
+    if (k >= 0 && k < nu) {
+        const float x = __ldg(Erow + k), fh = __ldg(fh_row + k);
+        p = x * fh;
+        c = fmaf(x, __ldg(fl_row + k), fmaf(x, fh, -p));
+    }
+}
+
+// First difference d(k) = w(k) - w(k-1) of rows [row0, row0 + nrows) split
+// into `planes` BF16 terms, ws[t][r][k] (k < kpad; zero beyond nu).  The
+// difference of the two double-floats is taken with a two-sum, then rounded
+// once to FP32.
 __global__ void __launch_bounds__(256)
     filter_split_kernel(const float *__restrict__ E, const float *__restrict__ fcos, const float *__restrict__ fcos_lo,
                         __nv_bfloat16 *ws, int nu, int nv, int kpad, long long row0, int nrows, int planes,
@@ -240,31 +248,31 @@ __global__ void __launch_bounds__(256)
     if (r >= nrows) return;
     const long long grow = row0 + r;
     const int v = (int)(grow % nv);
-    uint32_t w[4][4];
+    const float *Erow = E + grow * nu, *fh_row = fcos + (size_t)v * nu, *fl_row = fcos_lo + (size_t)v * nu;
+    float p0, c0;
+    weighted(Erow, fh_row, fl_row, k0 - 1, nu, p0, c0);
+    uint32_t w[3][4];
 #pragma unroll
     for (int q = 0; q < 8; q += 2) {
-        uint16_t h[4][2];
+        uint16_t h[3][2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int k = k0 + q + e;
-            float p = 0.0f, c = 0.0f;
-            if (k < nu) {
-                const float x = __ldg(E + grow * nu + k), fh = __ldg(fcos + (size_t)v * nu + k);
-                p = x * fh;
-                c = fmaf(x, __ldg(fcos_lo + (size_t)v * nu + k), fmaf(x, fh, -p));
-            }
-            float rem = p;
+            float p1, c1;
+            weighted(Erow, fh_row, fl_row, k0 + q + e, nu, p1, c1);
+            const float s = p1 - p0, bb = s - p1;
+            const float err = (p1 - (s - bb)) + (-p0 - bb);   // s + err = p1 - p0 exactly
+            float rem = s + (err + (c1 - c0));
+            p0 = p1;
+            c0 = c1;
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
                 const __nv_bfloat16 b = __float2bfloat16_rn(rem);
                 rem -= __bfloat162float(b);
                 h[t][e] = *reinterpret_cast<const uint16_t *>(&b);
             }
-            const __nv_bfloat16 b3 = __float2bfloat16_rn(c);
-            h[3][e] = *reinterpret_cast<const uint16_t *>(&b3);
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) w[t][q / 2] = (uint32_t)h[t][0] | ((uint32_t)h[t][1] << 16);
+        for (int t = 0; t < 3; ++t) w[t][q / 2] = (uint32_t)h[t][0] | ((uint32_t)h[t][1] << 16);
     }
     for (int t = 0; t < planes; ++t)
         *reinterpret_cast<uint4 *>(ws + t * plane + r * kpad + k0) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
@@ -300,8 +308,8 @@ int encode_bf16_3d(CUtensorMap *m, const void *base, uint64_t kpad, uint64_t row
                : IFDK_ERR_CUDA;
 }
 
-// Data planes of split s (3 terms use the 4-plane double-float form).
-int data_planes(int terms) { return terms == 3 ? 4 : terms; }
+// Data planes of split s.
+int data_planes(int terms) { return terms; }
 
 template <typename TQ>
 int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size_t ws_bytes, cudaStream_t stream)
@@ -326,7 +334,7 @@ int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size
     a.wait_ns = p->wait_ns;
     a.nu = g.nu;
     a.nk = kpad / kTcK;
-    a.npairs = terms == 3 ? 7 : (terms == 2 ? 3 : 1);
+    a.npairs = terms == 3 ? 6 : (terms == 2 ? 3 : 1);
     for (long long r0 = 0; r0 < rows; r0 += cap) {
         const int nr = (int)(rows - r0 < cap ? rows - r0 : cap);
         const long long threads = (long long)nr * (kpad / 8);
@@ -343,20 +351,25 @@ int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size
 
 }  // namespace
 
-// Plan-time part: the Toeplitz matrix T[n][k] = h(n - k) as three BF16 planes
-// (FP64 taps split term by term), zero outside nu x nu.
+// Plan-time part: the Toeplitz matrix G[n][k] = g(n - k) for n < nu, k <= nu
+// (g the running sum of the Ram-Lak taps, accumulated in FP64 from
+// m = -(nu-1); g(-nu) = 0) as three BF16 planes, each the rounded remainder
+// of the previous; zero elsewhere.
 int plan_filter_tc(ifdk_plan_s *p)
 {
     const int nu = p->g.nu;
-    p->tc_kpad = (nu + kTcK - 1) / kTcK * kTcK;
+    p->tc_kpad = (nu + 1 + kTcK - 1) / kTcK * kTcK;
     p->tc_npad = (nu + kTcN - 1) / kTcN * kTcN;
+    std::vector<double> gsum(2 * (size_t)nu, 0.0);   // gsum[m + nu] = g(m), m in [-nu, nu - 1]
+    for (int m = -nu + 1; m < nu; ++m) {
+        const double h = m == 0 ? 0.25 : ((m & 1) ? -1.0 / (M_PI * M_PI * (double)m * m) : 0.0);
+        gsum[m + nu] = gsum[m - 1 + nu] + h;
+    }
     const size_t plane = (size_t)p->tc_npad * p->tc_kpad;
     std::vector<uint16_t> t(3 * plane, 0);
     for (int n = 0; n < nu; ++n)
-        for (int k = 0; k < nu; ++k) {
-            const int m = n - k;
-            const double h = m == 0 ? 0.25 : ((m & 1) ? -1.0 / (M_PI * M_PI * (double)m * m) : 0.0);
-            double rem = h;
+        for (int k = 0; k <= nu; ++k) {
+            double rem = gsum[n - k + nu];
             for (int q = 0; q < 3; ++q) {
                 const uint16_t b = f2bf((float)rem);
                 t[q * plane + (size_t)n * p->tc_kpad + k] = b;

@@ -64,6 +64,7 @@ struct ifdk_plan_s {
     float *d_fcos = nullptr;             // [nv][nu]
     float *d_fcos_lo = nullptr;          // [nv][nu], F_cos - (float)F_cos
     float *d_taps = nullptr;             // [2 nu - 1], index m + nu - 1
+    float *d_gsum = nullptr;             // [2 nu], running tap sum g(m), index m + nu
     unsigned int *d_status = nullptr;    // device status word
     double uc = 0, vc = 0;               // principal point (pixels)
     int two_vc = 0;                      // 2 vc when it is an integer

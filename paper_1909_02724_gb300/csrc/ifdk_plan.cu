@@ -143,8 +143,10 @@ int ifdk_create(ifdk_plan *out, const ifdk_geometry *gin)
     if (rc != IFDK_OK) { delete p; return rc; }
     const ifdk_geometry &g = p->g;
 
-    // Cosine weight D / sqrt(D^2 + a^2 + b^2) and Ram-Lak taps, FP64 then FP32.
-    std::vector<float> fcos((size_t)g.nu * g.nv), fcos_lo(fcos.size()), taps(2 * (size_t)g.nu - 1);
+    // Cosine weight D / sqrt(D^2 + a^2 + b^2) (hi / lo FP32 pair), Ram-Lak
+    // taps h(m) and their running sum g(m) = sum_{j=-(nu-1)}^{m} h(j), FP64 then FP32.
+    std::vector<float> fcos((size_t)g.nu * g.nv), fcos_lo(fcos.size()), taps(2 * (size_t)g.nu - 1),
+        gsum(2 * (size_t)g.nu);
     for (int iv = 0; iv < g.nv; ++iv)
         for (int iu = 0; iu < g.nu; ++iu) {
             const double a = (iu - p->uc) * g.du, b = (iv - p->vc) * g.dv;
@@ -156,18 +158,26 @@ int ifdk_create(ifdk_plan *out, const ifdk_geometry *gin)
         const double h = m == 0 ? 0.25 : (m % 2 == 0 ? 0.0 : -1.0 / (M_PI * M_PI * (double)m * m));
         taps[m + g.nu - 1] = (float)h;
     }
+    double run = 0.0;   // g(-nu) = 0
+    gsum[0] = 0.0f;
+    for (int m = -(g.nu - 1); m <= g.nu - 1; ++m) {
+        run += m == 0 ? 0.25 : (m % 2 == 0 ? 0.0 : -1.0 / (M_PI * M_PI * (double)m * m));
+        gsum[m + g.nu] = (float)run;
+    }
 
     if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return IFDK_ERR_CUDA; }
     bool ok = cudaMalloc(&p->d_terms, sizeof(ViewTerms) * g.np) == cudaSuccess &&
               cudaMalloc(&p->d_fcos, sizeof(float) * fcos.size()) == cudaSuccess &&
               cudaMalloc(&p->d_fcos_lo, sizeof(float) * fcos.size()) == cudaSuccess &&
               cudaMalloc(&p->d_taps, sizeof(float) * taps.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_gsum, sizeof(float) * gsum.size()) == cudaSuccess &&
               cudaMalloc(&p->d_status, sizeof(unsigned int)) == cudaSuccess;
     if (!ok) { cudaGetLastError(); ifdk_destroy(p); return IFDK_ERR_NOMEM; }
     ok = cudaMemcpy(p->d_terms, p->terms.data(), sizeof(ViewTerms) * g.np, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(p->d_fcos, fcos.data(), sizeof(float) * fcos.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(p->d_fcos_lo, fcos_lo.data(), sizeof(float) * fcos.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(p->d_taps, taps.data(), sizeof(float) * taps.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(p->d_gsum, gsum.data(), sizeof(float) * gsum.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemset(p->d_status, 0, sizeof(unsigned int)) == cudaSuccess;
     if (!ok) { cudaGetLastError(); ifdk_destroy(p); return IFDK_ERR_CUDA; }
 
@@ -188,6 +198,7 @@ int ifdk_destroy(ifdk_plan p)
     cudaFree(p->d_fcos);
     cudaFree(p->d_fcos_lo);
     cudaFree(p->d_taps);
+    cudaFree(p->d_gsum);
     cudaFree(p->d_status);
     cudaFree(p->d_tsplit);
     if (dev >= 0 && dev != p->device) cudaSetDevice(dev);

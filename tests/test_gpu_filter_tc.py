@@ -1,8 +1,9 @@
 """The tensor-core filter (tcgen05 split-BF16 Toeplitz product) against the FP64 oracle.
 
-Expected accuracy from the operand splits (rel-L2 of Q): 3 terms ~1e-7 (FP32
-level), 2 terms ~1e-5, 1 term ~1e-2 (the ramp filter's cancellation of the
-large smooth part of each row amplifies operand rounding).  Sizes cover
+The kernel sums the convolution by parts (first differences of the weighted
+row against the running sum of the taps), so operand rounding is amplified
+only ~5x instead of the direct sum's ~1000x; expected rel-L2 of Q: 3 terms
+~1e-7 (FP32 level), 2 terms ~1e-6, 1 term ~1e-2.  Sizes cover
 ragged row counts, nu below / above / not a multiple of the 128-wide tile,
 and workspaces small enough to force many chunks."""
 import numpy as np
