@@ -10,6 +10,12 @@ volume, inputs resident in HBM.  The metric is GUPS = Nx*Ny*Nz*Np / (T * 2^30)
 reconstructs its own copy of the workload (independent problems: weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
 
+--workload slab4096 (not a default line) times the streamed large-slab case:
+a step back-projects the 2048 FP16 filtered views, held in pinned host memory
+(only the 272 detector rows the 4096 x 4096 x 256 central slab reads), into a
+zeroed slab, copying them to the device in 64-view chunks on a side stream
+while the back-projection runs; the copies are inside the timed region.
+
 --impl reference times the FP64 CPU oracle (the reference of this build) on
 the host cores, each step a bounded sample of the same workload.
 """
@@ -322,6 +328,97 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_slab(args):
+    """The streamed large-slab workload on one GPU (see the module docstring)."""
+    import torch
+    from paper_1909_02724_gb300 import binding as B
+    from paper_1909_02724_gb300.build import build
+    from paper_1909_02724_gb300.geometry import gups
+    from paper_1909_02724_gb300.phantom import line_integrals_gpu, workload
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return                      # one GPU: the other ranks have nothing to do
+    torch.cuda.set_device(local)
+    build()
+    w = workload(args.workload)
+    r0, n = B.ifdk_query_rows(w.geom)
+    g = w.geom.crop_rows(r0, n)     # the detector rows the slab reads
+    plan = B.Plan(g)
+    tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.dtype]
+    E = line_integrals_gpu(w.phantom(), g)
+    Qd = plan.filter(E, dtype=tdt)
+    del E
+    Qh = torch.empty(Qd.shape, dtype=tdt, pin_memory=True)
+    Qh.copy_(Qd)
+    chunk = 64
+    staging = torch.empty(2 * chunk * g.nv * g.nu, dtype=tdt, device="cuda")
+    vol = torch.empty((g.nx, g.ny, g.nz), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        vol.zero_()
+        plan.backproject_host(Qh, vol, staging, chunk_views=chunk)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    value = g.updates / (ms * 1e-3) / 2 ** 30
+    # the same back-projection from device-resident views (kernel only)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms = []
+    for _ in range(3):
+        vol.zero_()
+        k0.record(stream)
+        plan.backproject(Qd, vol)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        kms.append(k0.elapsed_time(k1))
+    bp_ms = float(np.median(kms))
+    # end to end: the streamed step plus reading the slab back to pinned host memory
+    vol_host = torch.empty(vol.shape, dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    step()
+    vol_host.copy_(vol, non_blocking=True)
+    torch.cuda.synchronize()
+    e_s = time.perf_counter() - a
+    props = torch.cuda.get_device_properties(torch.device("cuda", local))
+    peaks = measured_peaks()
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak_gups = props.multi_processor_count * 128 * f_max / FP32_OPS_PER_UPDATE / 2 ** 30
+    achieved = gups(g, bp_ms * 1e-3)
+    es = Qh.element_size()
+    line = {"metric": METRIC.replace("whole FDK step", "back-projection streamed from pinned host views"),
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": workload_desc(w) + f"; detector rows {r0}..{r0 + n - 1} of {w.geom.nv}",
+                       "storage": args.dtype, "accumulate": "f32", "chunk_views": chunk,
+                       "h2d_bytes_per_step": Qh.numel() * es, "l2": "inputs larger than L2",
+                       "bp_launch": plan.info(tdt)},
+            "kernel_only": {"value": achieved, "unit": UNIT, "bp_ms": bp_ms},
+            "e2e": {"value": g.updates / e_s / 2 ** 30, "unit": UNIT, "h2d_bytes_per_step": Qh.numel() * es,
+                    "d2h_bytes_per_step": vol.numel() * 4},
+            "gpu_launches": -(-g.np // chunk) * args.steps, "clocks": ck,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gups, "unit": UNIT,
+                         "frac": achieved / peak_gups, "traffic": None, "kernel": "bp_fold_kernel"},
+            "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(w, E, vol_gpu_unused, plan, Q):
     """The oracle on the host cores on a bounded sample (mid-plane slab), plus the
     accuracy of this run's GPU volume on the same voxels."""
@@ -357,6 +454,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "slab4096":
+        run_slab(args)
     else:
         run_ours(args)
 

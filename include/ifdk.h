@@ -163,6 +163,38 @@ int ifdk_filter_adjoint(ifdk_plan p, const float *G_Q, float *G_E, void *stream)
 int ifdk_backproject(ifdk_plan p, const void *Q, int q_dtype, int view_begin, int view_count,
                      float *vol, void *stream);
 
+/* ifdk_backproject with a buffer that holds only the called views: Qv is
+   device [view_count][nv][nu] of q_dtype, Qv[0] being view view_begin (the
+   paper's column decomposition, Sec. 4, where each worker holds a subset of
+   the views; also the staging chunks of ifdk_backproject_host).  Same
+   result, arithmetic and alignment rules as ifdk_backproject. */
+int ifdk_backproject_views(ifdk_plan p, const void *Qv, int q_dtype, int view_begin, int view_count,
+                           float *vol, void *stream);
+
+/* Back-projection of filtered views streamed from host memory (the paper's
+   Sec. 4 pipeline, where host-to-device transfer runs inside the
+   back-projection time): views [view_begin, view_begin + view_count) are
+   copied in chunks of chunk_views views into the two halves of `staging`
+   on a copy stream owned by the plan and back-projected on `stream` as each
+   chunk lands, so that the copy of chunk c+1 overlaps the back-projection
+   of chunk c (two events per half order the reuse).
+   Q_host: host array [np][host_nv][nu] of q_dtype whose rows
+   [host_row0, host_row0 + nv) are the plan's detector rows (host_nv = nv,
+   host_row0 = 0 when the host holds exactly the plan's detector; a plan
+   built for the rows a slab reads, see ifdk_query_rows, streams only those
+   rows out of full-height host views with one strided copy per chunk).
+   It should be page-locked (cudaHostAlloc / cudaHostRegister), or the copies
+   do not overlap.  staging: device, 256-byte aligned, at least
+   2 * chunk_views * nv * nu * sizeof(q_dtype) bytes, owned by the caller.
+   Asynchronous on `stream`: returns once everything is enqueued; Q_host,
+   staging and vol must stay untouched until `stream` has passed this work.
+   Copies start only after the work already on `stream`.  Calls on one plan
+   must be issued from one host thread at a time and, when they overlap, on
+   one stream (they share the plan's copy stream and events). */
+int ifdk_backproject_host(ifdk_plan p, const void *Q_host, int q_dtype, int host_nv, int host_row0,
+                          int view_begin, int view_count, int chunk_views, void *staging,
+                          size_t staging_bytes, float *vol, void *stream);
+
 /* Exact adjoint of ifdk_backproject (FP32): for every voxel, view in the
    range and bilinear tap, P[s][tap] += w_s f^2 (bilinear weight) vol[i][j][k].
    It is the transpose of the back-projection matrix, not a physical line-
@@ -199,6 +231,18 @@ int ifdk_backproject_info(ifdk_plan p, int q_dtype, int64_t info[8]);
    plus info[8] = fold width (elements) and info[9] = u alignment of the box
    start (elements).  Returns the geometry's validation status. */
 int ifdk_query_backproject(const ifdk_geometry *g, int q_dtype, int64_t info[10]);
+
+/* Host-only query: the detector rows [*row_begin, *row_begin + *row_count)
+   that back-projecting views [view_begin, view_begin + view_count) of this
+   geometry can read, from FP64 bounds of v over the volume (v - v_c is
+   (B2 k' + B3) / z with z affine in (i', j'), so its extremes sit at the
+   corners; Eq. 3, Theorems 2-3), widened by one row on each side and clipped
+   to the detector.  *row_count = 0 when no voxel projects onto the detector.
+   A plan whose detector is cut to these rows (nv = *row_count and
+   off_v shifted by ((nv_full - 1) / 2 - *row_begin - (*row_count - 1) / 2) * dv,
+   so that v_c moves by -*row_begin) back-projects the same volume. */
+int ifdk_query_rows(const ifdk_geometry *g, int view_begin, int view_count, int *row_begin,
+                    int *row_count);
 
 /* Human-readable text for a status code (static storage). */
 const char *ifdk_status_string(int code);

@@ -26,9 +26,9 @@ IFDK_ERR_TIMEOUT, IFDK_ERR_NOMEM, IFDK_ERR_UNSUPPORTED = -5, -6, -7
 # every symbol include/ifdk.h declares
 EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_size", "ifdk_filter_noalloc",
            "ifdk_filter_adjoint",
-           "ifdk_backproject",
+           "ifdk_backproject", "ifdk_backproject_views", "ifdk_backproject_host",
            "ifdk_project", "ifdk_last_device_status", "ifdk_set_wait_limit", "ifdk_wait_selftest",
-           "ifdk_backproject_info", "ifdk_query_backproject", "ifdk_status_string")
+           "ifdk_backproject_info", "ifdk_query_backproject", "ifdk_query_rows", "ifdk_status_string")
 
 
 class IfdkError(RuntimeError):
@@ -74,6 +74,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.ifdk_filter_noalloc.argtypes = [vp, vp, vp, i32, i32, vp]
         lib.ifdk_filter_adjoint.argtypes = [vp, vp, vp, vp]
         lib.ifdk_backproject.argtypes = [vp, vp, i32, i32, i32, vp, vp]
+        lib.ifdk_backproject_views.argtypes = [vp, vp, i32, i32, i32, vp, vp]
+        lib.ifdk_backproject_host.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, vp, ctypes.c_size_t, vp, vp]
+        lib.ifdk_query_rows.argtypes = [ctypes.POINTER(_GeometryC), i32, i32, ctypes.POINTER(i32),
+                                        ctypes.POINTER(i32)]
         lib.ifdk_project.argtypes = [vp, vp, vp, i32, i32, vp]
         lib.ifdk_last_device_status.argtypes = [vp, vp]
         lib.ifdk_set_wait_limit.argtypes = [vp, ctypes.c_uint64]
@@ -174,6 +178,32 @@ def ifdk_filter_adjoint(plan: int, G_Q, G_E, stream=None) -> None:
 def ifdk_backproject(plan: int, Q, q_dtype: int, view_begin: int, view_count: int, vol, stream=None) -> None:
     _check(load_library().ifdk_backproject(plan, _addr(Q), int(q_dtype), int(view_begin), int(view_count),
                                            _addr(vol), _stream(stream)), "ifdk_backproject")
+
+
+def ifdk_backproject_views(plan: int, Qv, q_dtype: int, view_begin: int, view_count: int, vol,
+                           stream=None) -> None:
+    """Qv holds only views [view_begin, view_begin + view_count)."""
+    _check(load_library().ifdk_backproject_views(plan, _addr(Qv), int(q_dtype), int(view_begin), int(view_count),
+                                                 _addr(vol), _stream(stream)), "ifdk_backproject_views")
+
+
+def ifdk_backproject_host(plan: int, Q_host, q_dtype: int, host_nv: int, host_row0: int, view_begin: int,
+                          view_count: int, chunk_views: int, staging, staging_bytes: int, vol, stream=None) -> None:
+    """Q_host: host address (or CPU tensor) of [np][host_nv][nu]; staging: device buffer."""
+    _check(load_library().ifdk_backproject_host(plan, _addr(Q_host), int(q_dtype), int(host_nv), int(host_row0),
+                                                int(view_begin), int(view_count), int(chunk_views), _addr(staging),
+                                                int(staging_bytes), _addr(vol), _stream(stream)),
+           "ifdk_backproject_host")
+
+
+def ifdk_query_rows(geom: Geometry, view_begin: int = 0, view_count: int | None = None) -> tuple[int, int]:
+    """Host-only: (row_begin, row_count) of the detector rows the volume reads."""
+    h = _GeomHolder(geom)
+    r0, n = ctypes.c_int32(), ctypes.c_int32()
+    vc = geom.np - view_begin if view_count is None else view_count
+    _check(load_library().ifdk_query_rows(ctypes.byref(h.c), int(view_begin), int(vc), ctypes.byref(r0),
+                                          ctypes.byref(n)), "ifdk_query_rows")
+    return int(r0.value), int(n.value)
 
 
 def ifdk_project(plan: int, vol, P, view_begin: int, view_count: int, stream=None) -> None:
@@ -291,6 +321,40 @@ class Plan:
         self._check_vol(vol)
         n = g.np - view_begin if view_count is None else view_count
         ifdk_backproject(self.handle, Q, dtype_code(Q.dtype), view_begin, n, vol, stream)
+        return vol
+
+    def backproject_views(self, Qv, vol=None, view_begin: int = 0, stream=None):
+        """Back-project a tensor that holds only views [view_begin, view_begin + len(Qv))."""
+        import torch
+        g = self.geom
+        if (not Qv.is_cuda or not Qv.is_contiguous() or Qv.dim() != 3 or tuple(Qv.shape[1:]) != (g.nv, g.nu)):
+            raise ValueError(f"Qv must be a contiguous CUDA tensor of shape (views, {g.nv}, {g.nu})")
+        if vol is None:
+            vol = torch.zeros((g.nx, g.ny, g.nz), dtype=torch.float32, device=Qv.device)
+        self._check_vol(vol)
+        ifdk_backproject_views(self.handle, Qv, dtype_code(Qv.dtype), view_begin, Qv.shape[0], vol, stream)
+        return vol
+
+    def backproject_host(self, Q_host, vol, staging=None, chunk_views: int = 64, host_row0: int = 0,
+                         view_begin: int = 0, view_count: int | None = None, stream=None):
+        """Back-project views streamed from a (pinned) CPU tensor [np][host_nv][nu]
+        whose rows [host_row0, host_row0 + nv) are this plan's detector.
+        staging: device buffer of >= 2 * chunk_views * nv * nu elements of
+        Q_host's dtype (allocated here if None).  Asynchronous on `stream`."""
+        import torch
+        g = self.geom
+        if (Q_host.is_cuda or not Q_host.is_contiguous() or Q_host.dim() != 3
+                or Q_host.shape[0] != g.np or Q_host.shape[2] != g.nu):
+            raise ValueError(f"Q_host must be a contiguous CPU tensor of shape ({g.np}, host_nv, {g.nu})")
+        self._check_vol(vol)
+        n = 2 * chunk_views * g.nv * g.nu
+        if staging is None:
+            staging = torch.empty(n, dtype=Q_host.dtype, device=vol.device)
+        if staging.dtype != Q_host.dtype or staging.numel() < n or not staging.is_cuda:
+            raise ValueError("staging must be a CUDA tensor of Q_host's dtype with >= 2 * chunk_views * nv * nu elements")
+        vc = g.np - view_begin if view_count is None else view_count
+        ifdk_backproject_host(self.handle, Q_host, dtype_code(Q_host.dtype), Q_host.shape[1], host_row0, view_begin,
+                              vc, chunk_views, staging, staging.numel() * staging.element_size(), vol, stream)
         return vol
 
     def project(self, vol, P=None, view_begin: int = 0, view_count: int | None = None, stream=None):

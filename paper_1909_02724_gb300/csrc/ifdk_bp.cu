@@ -47,7 +47,7 @@ struct BpArgs {
     unsigned int *status;
     unsigned long long wait_ns;
     int nx, ny, nz, tiles_x;
-    int view_begin, view_count;
+    int view_begin, view_count, q_view0;   // Q holds views from q_view0 on
     int box_w, box_h, fold_w, two_vc, views;
     float cx, cy, cz, uc, vc;
     uint32_t raw_box_bytes;    // one box, rounded up to 128 bytes
@@ -201,8 +201,8 @@ __device__ __forceinline__ void stage_chunk(const BpArgs &a, const Block &b, con
         for (int v = 0; v < nvc; ++v) {
             const int4 o = lds_i32x4(slot + v * (uint32_t)sizeof(ViewSmem) + 48);
             const uint32_t dst = raw_stage + 2u * v * a.raw_box_bytes;
-            tma_load_3d(dst, tmap, o.x, o.y, first_view + v, bar);
-            tma_load_3d(dst + a.raw_box_bytes, tmap, o.x, o.z, first_view + v, bar);
+            tma_load_3d(dst, tmap, o.x, o.y, first_view + v - a.q_view0, bar);
+            tma_load_3d(dst + a.raw_box_bytes, tmap, o.x, o.z, first_view + v - a.q_view0, bar);
         }
     }
 }
@@ -457,7 +457,7 @@ struct GenArgs {
     const void *Q;
     const ViewTerms *terms;
     int nx, ny, nz, nu, nv, tiles_x;
-    int view_begin, view_count;
+    int view_begin, view_count, q_view0;   // Q holds views from q_view0 on
     float cx, cy, cz, uc, vc;
 };
 
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(kThreads) bp_general_kernel(const GenArgs a)
         const float W = t2.x * f * f;
         const float sig = t0.w * f;
         const float vb = fmaf(t1.x, f, a.vc);
-        const T *Qs = Q + (size_t)s * a.nv * a.nu;
+        const T *Qs = Q + (size_t)(s - a.q_view0) * a.nv * a.nu;
 #pragma unroll
         for (int zz = 0; zz < kGenZ; ++zz) {
             const float v = fmaf((float)(kb + zz) - a.cz, sig, vb);
@@ -559,15 +559,15 @@ BpLaunch size_pairs(const ifdk_plan_s *p, int q_dtype)
 }
 
 template <typename T>
-int launch_pairs(ifdk_plan_s *p, const BpLaunch &b, const void *Q, int view_begin, int view_count, float *vol,
-                 cudaStream_t stream)
+int launch_pairs(ifdk_plan_s *p, const BpLaunch &b, const void *Q, int view_begin, int view_count, int q_view0,
+                 int q_views, float *vol, cudaStream_t stream)
 {
     const ifdk_geometry &g = p->g;
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return IFDK_ERR_CUDA;
     const int es = sizeof(T);
     CUtensorMap tmap;
-    const cuuint64_t dims[3] = {(cuuint64_t)g.nu, (cuuint64_t)g.nv, (cuuint64_t)g.np};
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nu, (cuuint64_t)g.nv, (cuuint64_t)q_views};
     const cuuint64_t strides[2] = {(cuuint64_t)g.nu * es, (cuuint64_t)g.nu * g.nv * es};
     const cuuint32_t box[3] = {(cuuint32_t)b.box_w, (cuuint32_t)b.box_h, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
@@ -584,6 +584,7 @@ int launch_pairs(ifdk_plan_s *p, const BpLaunch &b, const void *Q, int view_begi
     a.tiles_x = (g.nx + kTileX - 1) / kTileX;
     a.view_begin = view_begin;
     a.view_count = view_count;
+    a.q_view0 = q_view0;
     a.box_w = b.box_w; a.box_h = b.box_h; a.fold_w = b.fold_w;
     a.two_vc = p->two_vc;
     a.views = b.views;
@@ -600,7 +601,7 @@ int launch_pairs(ifdk_plan_s *p, const BpLaunch &b, const void *Q, int view_begi
 }
 
 template <typename T>
-int launch_general(ifdk_plan_s *p, const void *Q, int view_begin, int view_count, float *vol,
+int launch_general(ifdk_plan_s *p, const void *Q, int view_begin, int view_count, int q_view0, float *vol,
                    cudaStream_t stream)
 {
     const ifdk_geometry &g = p->g;
@@ -608,7 +609,7 @@ int launch_general(ifdk_plan_s *p, const void *Q, int view_begin, int view_count
     a.vol = vol; a.Q = Q; a.terms = p->d_terms;
     a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.nu = g.nu; a.nv = g.nv;
     a.tiles_x = (g.nx + kTileX - 1) / kTileX;
-    a.view_begin = view_begin; a.view_count = view_count;
+    a.view_begin = view_begin; a.view_count = view_count; a.q_view0 = q_view0;
     a.cx = (float)((g.nx - 1) / 2.0); a.cy = (float)((g.ny - 1) / 2.0); a.cz = (float)((g.nz - 1) / 2.0);
     a.uc = (float)p->uc; a.vc = (float)p->vc;
     const int tiles_y = (g.ny + kTileY - 1) / kTileY;
@@ -632,23 +633,23 @@ void plan_backproject(ifdk_plan_s *p)
     }
 }
 
-int launch_backproject(ifdk_plan_s *p, const void *Q, int q_dtype, int view_begin, int view_count,
-                       float *vol, cudaStream_t stream)
+int launch_backproject(ifdk_plan_s *p, const void *Q, int q_dtype, int view_begin, int view_count, int q_view0,
+                       int q_views, float *vol, cudaStream_t stream)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return IFDK_ERR_CUDA;
     const BpLaunch &b = p->bp[q_dtype];
     if (b.path == 1) {
         switch (q_dtype) {
-        case IFDK_F32: return launch_pairs<float>(p, b, Q, view_begin, view_count, vol, stream);
-        case IFDK_F16: return launch_pairs<__half>(p, b, Q, view_begin, view_count, vol, stream);
-        default: return launch_pairs<__nv_bfloat16>(p, b, Q, view_begin, view_count, vol, stream);
+        case IFDK_F32: return launch_pairs<float>(p, b, Q, view_begin, view_count, q_view0, q_views, vol, stream);
+        case IFDK_F16: return launch_pairs<__half>(p, b, Q, view_begin, view_count, q_view0, q_views, vol, stream);
+        default: return launch_pairs<__nv_bfloat16>(p, b, Q, view_begin, view_count, q_view0, q_views, vol, stream);
         }
     }
     switch (q_dtype) {
-    case IFDK_F32: return launch_general<float>(p, Q, view_begin, view_count, vol, stream);
-    case IFDK_F16: return launch_general<__half>(p, Q, view_begin, view_count, vol, stream);
-    default: return launch_general<__nv_bfloat16>(p, Q, view_begin, view_count, vol, stream);
+    case IFDK_F32: return launch_general<float>(p, Q, view_begin, view_count, q_view0, vol, stream);
+    case IFDK_F16: return launch_general<__half>(p, Q, view_begin, view_count, q_view0, vol, stream);
+    default: return launch_general<__nv_bfloat16>(p, Q, view_begin, view_count, q_view0, vol, stream);
     }
 }
 

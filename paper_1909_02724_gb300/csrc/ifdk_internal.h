@@ -75,13 +75,18 @@ struct ifdk_plan_s {
     int tc_kpad = 0, tc_npad = 0;
     uint16_t *d_tsplit = nullptr;
     CUtensorMap tc_tmap_b;
+    // host streaming (ifdk_backproject_host): copy stream and, per staging
+    // half, "copy landed" and "back-projection done" events
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copy[2] = {nullptr, nullptr}, ev_bp[2] = {nullptr, nullptr}, ev_start = nullptr;
 };
 
 // Implemented in ifdk_bp.cu / ifdk_filter.cu / ifdk_project.cu.
 namespace ifdk {
 void plan_backproject(ifdk_plan_s *p);
-int launch_backproject(ifdk_plan_s *p, const void *Q, int q_dtype, int view_begin, int view_count,
-                       float *vol, cudaStream_t stream);
+// Q holds views [q_view0, q_view0 + q_views) of [nv][nu] each.
+int launch_backproject(ifdk_plan_s *p, const void *Q, int q_dtype, int view_begin, int view_count, int q_view0,
+                       int q_views, float *vol, cudaStream_t stream);
 int launch_filter(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int split_terms, bool adjoint,
                   cudaStream_t stream);
 int plan_filter_tc(ifdk_plan_s *p);
@@ -91,4 +96,6 @@ int launch_filter_tc(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int t
 int launch_project(ifdk_plan_s *p, const float *vol, float *P, int view_begin, int view_count,
                    cudaStream_t stream);
 int launch_wait_selftest(ifdk_plan_s *p, unsigned long long ns, cudaStream_t stream);
+int check_backproject_args(const ifdk_plan_s *p, const void *Q, int q_dtype, int view_begin, int view_count,
+                           const float *vol);
 }  // namespace ifdk

@@ -3,6 +3,7 @@
 // The plan forms every geometric quantity in FP64 (Eq. 2 projection terms,
 // FDK view weights, the F_cos table and the Ram-Lak taps of Algorithm 1) and
 // casts the results to FP32 device tables: these are the only FP64 steps.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -109,6 +110,18 @@ int init_host_plan(ifdk_plan_s *p, const ifdk_geometry *gin)
 }
 
 }  // namespace
+
+int check_backproject_args(const ifdk_plan_s *p, const void *Q, int q_dtype, int view_begin, int view_count,
+                           const float *vol)
+{
+    if (!p || !Q || !vol) return IFDK_ERR_INVALID;
+    if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
+    if (view_begin < 0 || view_count < 0 || view_begin > p->g.np || view_count > p->g.np - view_begin)
+        return IFDK_ERR_INVALID;
+    if (((uintptr_t)Q & 15) || ((uintptr_t)vol & 15)) return IFDK_ERR_ALIGNMENT;
+    return IFDK_OK;
+}
+
 }  // namespace ifdk
 
 using namespace ifdk;
@@ -183,6 +196,12 @@ int ifdk_create(ifdk_plan *out, const ifdk_geometry *gin)
 
     rc = plan_filter_tc(p);
     if (rc != IFDK_OK) { cudaGetLastError(); ifdk_destroy(p); return rc; }
+    ok = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = cudaEventCreateWithFlags(&p->ev_copy[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p->ev_bp[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); ifdk_destroy(p); return IFDK_ERR_CUDA; }
     plan_backproject(p);
     *out = p;
     return IFDK_OK;
@@ -194,6 +213,9 @@ int ifdk_destroy(ifdk_plan p)
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != p->device) cudaSetDevice(p->device);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    for (cudaEvent_t e : {p->ev_start, p->ev_copy[0], p->ev_copy[1], p->ev_bp[0], p->ev_bp[1]})
+        if (e) cudaEventDestroy(e);
     cudaFree(p->d_terms);
     cudaFree(p->d_fcos);
     cudaFree(p->d_fcos_lo);
@@ -240,13 +262,18 @@ int ifdk_filter_adjoint(ifdk_plan p, const float *G_Q, float *G_E, void *stream)
 int ifdk_backproject(ifdk_plan p, const void *Q, int q_dtype, int view_begin, int view_count,
                      float *vol, void *stream)
 {
-    if (!p || !Q || !vol) return IFDK_ERR_INVALID;
-    if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
-    if (view_begin < 0 || view_count < 0 || view_begin > p->g.np || view_count > p->g.np - view_begin)
-        return IFDK_ERR_INVALID;
-    if (((uintptr_t)Q & 15) || ((uintptr_t)vol & 15)) return IFDK_ERR_ALIGNMENT;
-    if (view_count == 0) return IFDK_OK;
-    return launch_backproject(p, Q, q_dtype, view_begin, view_count, vol, (cudaStream_t)stream);
+    const int rc = check_backproject_args(p, Q, q_dtype, view_begin, view_count, vol);
+    if (rc != IFDK_OK || view_count == 0) return rc;
+    return launch_backproject(p, Q, q_dtype, view_begin, view_count, 0, p->g.np, vol, (cudaStream_t)stream);
+}
+
+int ifdk_backproject_views(ifdk_plan p, const void *Qv, int q_dtype, int view_begin, int view_count,
+                           float *vol, void *stream)
+{
+    const int rc = check_backproject_args(p, Qv, q_dtype, view_begin, view_count, vol);
+    if (rc != IFDK_OK || view_count == 0) return rc;
+    return launch_backproject(p, Qv, q_dtype, view_begin, view_count, view_begin, view_count, vol,
+                              (cudaStream_t)stream);
 }
 
 int ifdk_project(ifdk_plan p, const float *vol, float *P, int view_begin, int view_count, void *stream)
@@ -302,6 +329,43 @@ int ifdk_backproject_info(ifdk_plan p, int q_dtype, int64_t info[8])
     if (!p || !info) return IFDK_ERR_INVALID;
     if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
     fill_info(p, p->bp[q_dtype], info);
+    return IFDK_OK;
+}
+
+int ifdk_query_rows(const ifdk_geometry *g, int view_begin, int view_count, int *row_begin, int *row_count)
+{
+    if (!row_begin || !row_count) return IFDK_ERR_INVALID;
+    int rc = validate(g);
+    if (rc != IFDK_OK) return rc;
+    if (view_begin < 0 || view_count < 0 || view_begin > g->np || view_count > g->np - view_begin)
+        return IFDK_ERR_INVALID;
+    ifdk_plan_s tmp;
+    rc = init_host_plan(&tmp, g);
+    if (rc != IFDK_OK) return rc;
+    const double cx = (g->nx - 1) / 2.0, cy = (g->ny - 1) / 2.0, cz = (g->nz - 1) / 2.0;
+    double vmin = 1e300, vmax = -1e300;
+    for (int s = view_begin; s < view_begin + view_count; ++s) {
+        const double cb = std::cos(g->angles[s]), sb = std::sin(g->angles[s]);
+        for (int q = 0; q < 4; ++q) {
+            const double ip = (q & 1) ? cx : -cx, jp = (q & 2) ? cy : -cy;
+            const double z = g->sid + g->dx * sb * ip - g->dy * cb * jp;   // homogeneous z at a column corner
+            for (int e = 0; e < 2; ++e) {
+                const double kp = e ? cz : -cz;
+                const double v = tmp.vc + (g->sdd * g->dz * kp - g->sdd * g->vol_off_z) / (g->dv * z);
+                vmin = std::min(vmin, v);
+                vmax = std::max(vmax, v);
+            }
+        }
+    }
+    *row_begin = 0;
+    *row_count = 0;
+    if (view_count == 0) return IFDK_OK;
+    // taps floor(v) and floor(v) + 1, one more row on each side for FP32 rounding
+    const double lo = std::floor(vmin) - 1.0, hi = std::floor(vmax) + 2.0;
+    if (hi < 0.0 || lo > g->nv - 1.0) return IFDK_OK;
+    const int r0 = (int)std::max(lo, 0.0), r1 = (int)std::min(hi, g->nv - 1.0);
+    *row_begin = r0;
+    *row_count = r1 - r0 + 1;
     return IFDK_OK;
 }
 

@@ -52,6 +52,15 @@ class Geometry:
     def with_(self, **kw) -> "Geometry":
         return replace(self, **kw)
 
+    def crop_rows(self, row_begin: int, row_count: int) -> "Geometry":
+        """The same scanner with the detector cut to rows [row_begin, row_begin + row_count):
+        the principal point moves by -row_begin rows, so every voxel projects onto
+        the same physical pixel (and the cosine weight is unchanged)."""
+        if row_count < 1 or row_begin < 0 or row_begin + row_count > self.nv:
+            raise ValueError("row window outside the detector")
+        off_v = self.off_v + ((self.nv - 1) / 2.0 - row_begin - (row_count - 1) / 2.0) * self.dv
+        return replace(self, nv=row_count, off_v=off_v)
+
 
 def circular(n_views: int, nu: int, nv: int, du: float, dv: float, nx: int, ny: int, nz: int,
              dx: float, dy: float | None = None, dz: float | None = None, sid: float = 1000.0,
