@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--no-view-pairing", action="store_true",
+                    help="back-project every view singly (no half-turn view pairs)")
+    ap.add_argument("--standard", action="store_true",
+                    help="back-project the filtered views as filtered (ifdk_backproject), not packed")
     return ap.parse_args()
 
 
@@ -119,10 +123,11 @@ def measured_peaks():
         return {}
 
 
-def profile_traffic(kernel_file: str, workload: str):
+def profile_traffic(kernel_file: str, prof: str):
     """DRAM bytes per launch of the back-projection kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"bp_fold_{workload}.json")
+    summary profiles/<prof>.json, if it was taken on the current kernel source
+    (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{prof}.json")
     try:
         with open(path) as f:
             prof = json.load(f)
@@ -217,19 +222,27 @@ def run_ours(args):
     g = w.geom
     tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.dtype]
     plan = B.Plan(g)
-    info = plan.info(tdt)
+    plan.set_view_pairing(not args.no_view_pairing)
+    packed = not args.standard and plan.has_packed(tdt)
+    info = plan.packed_info(tdt) if packed else plan.info(tdt)
     dev = torch.device("cuda", local)
     E = workload_projections_gpu(w)
     Q = torch.empty((g.np, g.nv, g.nu), dtype=tdt, device=dev)
+    Qp = torch.empty(plan.packed_shape(tdt), dtype=tdt, device=dev) if packed else None
     vol = torch.empty((g.nx, g.ny, g.nz), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
     def step(ev_bp=None):
         vol.zero_()
         plan.filter(E, Q)
+        if packed:
+            plan.pack(Q, Qp)
         if ev_bp is not None:
             ev_bp[0].record(stream)
-        plan.backproject(Q, vol)
+        if packed:
+            plan.backproject_packed(Qp, vol)
+        else:
+            plan.backproject(Q, vol)
         if ev_bp is not None:
             ev_bp[1].record(stream)
 
@@ -264,10 +277,11 @@ def run_ours(args):
     value = world * g.updates * args.steps / (ms * 1e-3) / 2 ** 30
 
     # launches of our kernels per step: tensor-core filter (a split pre-pass and a GEMM per
-    # chunk of up to 16384 rows, the preferred workspace) + 1 back-projection
+    # chunk of up to 16384 rows, the preferred workspace), the pack (packed path) and
+    # one back-projection (the full scan pairs up, or is one range of single views)
     rows = g.np * g.nv
     cap = min(16384, -(-rows // 128) * 128)
-    launches = (2 * -(-rows // cap) + 1) * args.steps
+    launches = (2 * -(-rows // cap) + (2 if packed else 1)) * args.steps
 
     # end to end through host buffers (pinned), copies inside the timed region
     e2e = None
@@ -277,13 +291,13 @@ def run_ours(args):
         vol_host = torch.empty(vol.shape, dtype=torch.float32, pin_memory=True)
         e_steps = max(3, min(args.steps, 10))
         for _ in range(2):
-            fdk_host(plan, E_host, vol_host, E, Q, vol)
+            fdk_host(plan, E_host, vol_host, E, Q, vol, Qp_dev=Qp)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         a = time.perf_counter()
         for _ in range(e_steps):
-            fdk_host(plan, E_host, vol_host, E, Q, vol)
+            fdk_host(plan, E_host, vol_host, E, Q, vol, Qp_dev=Qp)
         e_s = torch.tensor([time.perf_counter() - a], device=dev)
         if world > 1:
             dist.all_reduce(e_s, op=dist.ReduceOp.MAX)
@@ -301,9 +315,15 @@ def run_ours(args):
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak_gups = n_sm * 128 * f_max / FP32_OPS_PER_UPDATE / 2 ** 30
     achieved = gups(g, bp_ms * 1e-3)
+    if packed:
+        kname, kfile = "bp_packed_kernel", "ifdk_bp_packed.cu"
+        prof = f"bp_packed_{args.workload}_{args.dtype}" + ("" if info["path"] == 2 else "_single")
+    else:
+        kname = "bp_pairs_fold_kernel" if info["path"] == 1 else "bp_general_kernel"
+        kfile, prof = "ifdk_bp.cu", f"bp_fold_{args.workload}"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gups, "unit": UNIT,
-                "frac": achieved / peak_gups, "traffic": profile_traffic("ifdk_bp.cu", args.workload),
-                "kernel": "bp_fold_kernel" if info["path"] == 1 else "bp_general_kernel",
+                "frac": achieved / peak_gups, "traffic": profile_traffic(kfile, prof),
+                "kernel": kname,
                 "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz (MEASURED_PEAKS sm_max_mhz) "
                               f"/ {FP32_OPS_PER_UPDATE} FP32 ops per update",
                 "frac_at_sampled_clock": (achieved / (peak_gups * ck["sm_mhz"] * 1e6 / f_max)
@@ -320,6 +340,8 @@ def run_ours(args):
             "config": {"workload": workload_desc(w), "storage": args.dtype, "accumulate": "f32",
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (E, Q, vol each >= 256 MiB)",
+                       "bp_path": ("packed views" + (", half-turn view pairs" if info["path"] == 2 else ""))
+                       if packed else "filtered views as stored",
                        "bp_launch": info},
             "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roofline,
             "cpu_baseline": cpu}
@@ -351,14 +373,16 @@ def run_slab(args):
     del E
     Qh = torch.empty(Qd.shape, dtype=tdt, pin_memory=True)
     Qh.copy_(Qd)
+    plan.set_view_pairing(not args.no_view_pairing)
     chunk = 64
-    staging = torch.empty(2 * chunk * g.nv * g.nu, dtype=tdt, device="cuda")
+    packed = not args.standard and plan.has_packed(tdt)
+    staging = torch.empty(plan.staging_elems(tdt, chunk, packed), dtype=tdt, device="cuda")
     vol = torch.empty((g.nx, g.ny, g.nz), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
         vol.zero_()
-        plan.backproject_host(Qh, vol, staging, chunk_views=chunk)
+        plan.backproject_host(Qh, vol, staging, chunk_views=chunk, packed=packed)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -377,15 +401,20 @@ def run_slab(args):
     ms = t0.elapsed_time(t1) / args.steps
     value = g.updates / (ms * 1e-3) / 2 ** 30
     # the same back-projection from device-resident views (kernel only)
+    Qpd = plan.pack(Qd) if packed else None
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kms = []
     for _ in range(3):
         vol.zero_()
         k0.record(stream)
-        plan.backproject(Qd, vol)
+        if packed:
+            plan.backproject_packed(Qpd, vol)
+        else:
+            plan.backproject(Qd, vol)
         k1.record(stream)
         torch.cuda.synchronize()
         kms.append(k0.elapsed_time(k1))
+    del Qpd
     bp_ms = float(np.median(kms))
     # end to end: the streamed step plus reading the slab back to pinned host memory
     vol_host = torch.empty(vol.shape, dtype=torch.float32, pin_memory=True)
@@ -408,13 +437,17 @@ def run_slab(args):
             "config": {"workload": workload_desc(w) + f"; detector rows {r0}..{r0 + n - 1} of {w.geom.nv}",
                        "storage": args.dtype, "accumulate": "f32", "chunk_views": chunk,
                        "h2d_bytes_per_step": Qh.numel() * es, "l2": "inputs larger than L2",
-                       "bp_launch": plan.info(tdt)},
+                       "bp_path": ("views packed per chunk on the device" +
+                                   (", half-turn view pairs" if plan.packed_info(tdt)["path"] == 2 else ""))
+                       if packed else "filtered views as stored",
+                       "bp_launch": plan.packed_info(tdt) if packed else plan.info(tdt)},
             "kernel_only": {"value": achieved, "unit": UNIT, "bp_ms": bp_ms},
             "e2e": {"value": g.updates / e_s / 2 ** 30, "unit": UNIT, "h2d_bytes_per_step": Qh.numel() * es,
                     "d2h_bytes_per_step": vol.numel() * 4},
-            "gpu_launches": -(-g.np // chunk) * args.steps, "clocks": ck,
+            "gpu_launches": (2 if packed else 1) * -(-g.np // chunk) * args.steps, "clocks": ck,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gups, "unit": UNIT,
-                         "frac": achieved / peak_gups, "traffic": None, "kernel": "bp_fold_kernel"},
+                         "frac": achieved / peak_gups, "traffic": None,
+                         "kernel": "bp_packed_kernel" if packed else "bp_pairs_fold_kernel"},
             "cpu_baseline": None}
     print(json.dumps(line), flush=True)
 

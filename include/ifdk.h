@@ -171,6 +171,74 @@ int ifdk_backproject(ifdk_plan p, const void *Q, int q_dtype, int view_begin, in
 int ifdk_backproject_views(ifdk_plan p, const void *Qv, int q_dtype, int view_begin, int view_count,
                            float *vol, void *stream);
 
+/* Packed views: the filtered views rearranged for the mirror-pair back-
+   projection (Theorem 1 pairs voxel k with voxel nz-1-k, whose detector rows
+   are mirror images about v_c: v_mirror = 2 v_c - v).  Available when the
+   volume is centred on the source plane (vol_off_z = 0) and 2 v_c is an
+   integer (v_c = (nv-1)/2 + off_v/dv); otherwise these calls return
+   IFDK_ERR_UNSUPPORTED and ifdk_backproject serves every geometry.
+   A packed view is [rows][row_elems][4] of q_dtype: element (i, e), for
+   i in [0, rows) and e in [0, row_elems), is detector row r = r0 + i with
+   r0 = min(0, 2 v_c - (nv - 1)) (rows = floor(v_c) + 3 - r0) and column
+   c = e - 1 (row_elems = nu + 1 rounded up to even) and holds
+     Q[r][c], Q[2 v_c - r][c], Q[r][c + 1], Q[2 v_c - r][c + 1],
+   each 0 where its row or column is outside the detector.  That is about
+   twice the bytes of a view of Q, and one shared-memory load then gives a
+   voxel pair both taps of a detector row.
+   ifdk_packed_size reports view_bytes (bytes of one packed view), rows and
+   row_elems (any pointer may be NULL). */
+int ifdk_packed_size(ifdk_plan p, int q_dtype, size_t *view_bytes, int *rows, int *row_elems);
+
+/* Packs view_count views: Q device [view_count][nv][nu] of q_dtype ->
+   Qp device [view_count][rows][row_elems][4] of q_dtype (ifdk_packed_size),
+   both 16-byte aligned, not overlapping.  One memory-bound pass (each value
+   of Q is read twice and written twice).  Asynchronous on `stream`. */
+int ifdk_pack_views(ifdk_plan p, const void *Q, int q_dtype, int view_count, void *Qp, void *stream);
+
+/* Back-projection (Algorithm 4, the same sum as ifdk_backproject) from packed
+   views: Qp device [np][rows][row_elems][4] of q_dtype (all views packed,
+   ifdk_pack_views), 16-byte aligned; views [view_begin, view_begin +
+   view_count) are added into vol (device FP32 [nx][ny][nz], 16-byte
+   aligned).  TMA stages windows of packed views in shared memory as they
+   are used (a ring of stages paced by mbarriers).  With half-turn view
+   pairing (ifdk_set_view_pairing) the views of the range that pair up are
+   back-projected together.  The fast path for FDK: ifdk_filter,
+   ifdk_pack_views, ifdk_backproject_packed. */
+int ifdk_backproject_packed(ifdk_plan p, const void *Qp, int q_dtype, int view_begin, int view_count,
+                            float *vol, void *stream);
+
+/* Half-turn view pairing of ifdk_backproject_packed and of the packed
+   streaming path of ifdk_backproject_host (on by default).  When the scan
+   holds, for every view s < np/2, the view s + np/2 turned by exactly pi
+   (checked in FP64 at ifdk_create, e.g. any uniform full scan with even np)
+   and ny is even, voxel (X, Y, Z) in view s and voxel (-X, -Y, Z) in view
+   s + np/2 project to the same detector point (u, v) with the same z (Eq. 2:
+   Mrot(b + pi) = -Mrot(b) in the XY plane).  A thread then owns columns
+   (i, j) and (nx-1-i, ny-1-j) and each evaluation of the coordinates of
+   Algorithm 4 serves four voxels: (i, j, k), (i, j, nz-1-k),
+   (nx-1-i, ny-1-j, k), (nx-1-i, ny-1-j, nz-1-k), of the two views.  Same
+   sum, different FP32 rounding order.  (The paper's Sec. 3.2 cites this
+   kind of rotational symmetry, after Zhao et al., and leaves it out because
+   its pipeline receives views in scan order.)  Views of a call whose partner
+   is outside the call's view range are back-projected singly.
+   enable = 0 turns pairing off for this plan, 1 back on. */
+int ifdk_set_view_pairing(ifdk_plan p, int enable);
+
+/* Describes a full-range ifdk_backproject_packed launch with q_dtype:
+   info[0] = path (2 = half-turn view pairs, 1 = single views, 0 = packed
+   path not available), info[1] = TMA box width (elements), info[2] = box
+   height (rows), info[3] = z pairs per thread, info[4] = TMA stages,
+   info[5] = dynamic shared memory bytes per block, info[6] = blocks in the
+   grid, info[7] = window width (pixels), info[8] = u alignment of the box
+   start (pixels), info[9] = packed rows, info[10] = packed row elements,
+   info[11] = r0, the detector row of packed row 0. */
+int ifdk_backproject_packed_info(ifdk_plan p, int q_dtype, int64_t info[12]);
+
+/* Host-only query (no device needed): ifdk_backproject_packed_info for this
+   geometry and q_dtype with half-turn pairing on (view_pairing = 1) or off
+   (0).  Returns the geometry's validation status. */
+int ifdk_query_packed(const ifdk_geometry *g, int q_dtype, int view_pairing, int64_t info[12]);
+
 /* Back-projection of filtered views streamed from host memory (the paper's
    Sec. 4 pipeline, where host-to-device transfer runs inside the
    back-projection time): views [view_begin, view_begin + view_count) are
@@ -186,6 +254,13 @@ int ifdk_backproject_views(ifdk_plan p, const void *Qv, int q_dtype, int view_be
    It should be page-locked (cudaHostAlloc / cudaHostRegister), or the copies
    do not overlap.  staging: device, 256-byte aligned, at least
    2 * chunk_views * nv * nu * sizeof(q_dtype) bytes, owned by the caller.
+   With packed views available (ifdk_packed_size) and staging of at least
+   2 * chunk_views * (nv * nu * sizeof(q_dtype) + packed view_bytes) bytes,
+   each chunk is packed on `stream` into the second part of the staging and
+   back-projected by the kernels of ifdk_backproject_packed; with half-turn
+   view pairing, the views that pair up travel first, in chunks of
+   chunk_views / 2 views with their partners (two copies per chunk).
+   Otherwise the kernels of ifdk_backproject read the chunks as copied.
    Asynchronous on `stream`: returns once everything is enqueued; Q_host,
    staging and vol must stay untouched until `stream` has passed this work.
    Copies start only after the work already on `stream`.  Calls on one plan

@@ -19,6 +19,7 @@ _LIBDIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib")
 LIB_PATH = os.path.join(_LIBDIR, "libifdk.so")
 
 IFDK_F32, IFDK_F16, IFDK_BF16 = 0, 1, 2
+_ELEM = {0: 4, 1: 2, 2: 2}   # bytes per element of each storage type
 IFDK_OK = 0
 IFDK_ERR_INVALID, IFDK_ERR_GEOMETRY, IFDK_ERR_ALIGNMENT, IFDK_ERR_CUDA = -1, -2, -3, -4
 IFDK_ERR_TIMEOUT, IFDK_ERR_NOMEM, IFDK_ERR_UNSUPPORTED = -5, -6, -7
@@ -28,7 +29,9 @@ EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_
            "ifdk_filter_adjoint",
            "ifdk_backproject", "ifdk_backproject_views", "ifdk_backproject_host",
            "ifdk_project", "ifdk_last_device_status", "ifdk_set_wait_limit", "ifdk_wait_selftest",
-           "ifdk_backproject_info", "ifdk_query_backproject", "ifdk_query_rows", "ifdk_status_string")
+           "ifdk_backproject_info", "ifdk_query_backproject", "ifdk_query_rows", "ifdk_status_string",
+           "ifdk_packed_size", "ifdk_pack_views", "ifdk_backproject_packed", "ifdk_set_view_pairing",
+           "ifdk_backproject_packed_info", "ifdk_query_packed")
 
 
 class IfdkError(RuntimeError):
@@ -84,6 +87,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.ifdk_wait_selftest.argtypes = [vp, ctypes.c_uint64, vp]
         lib.ifdk_backproject_info.argtypes = [vp, i32, ctypes.POINTER(i64)]
         lib.ifdk_query_backproject.argtypes = [ctypes.POINTER(_GeometryC), i32, ctypes.POINTER(i64)]
+        lib.ifdk_packed_size.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i32),
+                                         ctypes.POINTER(i32)]
+        lib.ifdk_pack_views.argtypes = [vp, vp, i32, i32, vp, vp]
+        lib.ifdk_backproject_packed.argtypes = [vp, vp, i32, i32, i32, vp, vp]
+        lib.ifdk_set_view_pairing.argtypes = [vp, i32]
+        lib.ifdk_backproject_packed_info.argtypes = [vp, i32, ctypes.POINTER(i64)]
+        lib.ifdk_query_packed.argtypes = [ctypes.POINTER(_GeometryC), i32, i32, ctypes.POINTER(i64)]
         lib.ifdk_status_string.argtypes = [i32]
         lib.ifdk_status_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -204,6 +214,48 @@ def ifdk_query_rows(geom: Geometry, view_begin: int = 0, view_count: int | None 
     _check(load_library().ifdk_query_rows(ctypes.byref(h.c), int(view_begin), int(vc), ctypes.byref(r0),
                                           ctypes.byref(n)), "ifdk_query_rows")
     return int(r0.value), int(n.value)
+
+
+def ifdk_packed_size(plan: int, q_dtype: int) -> tuple[int, int, int]:
+    """(bytes of one packed view, packed rows, elements per packed row)."""
+    vb, rows, re = ctypes.c_size_t(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().ifdk_packed_size(plan, int(q_dtype), ctypes.byref(vb), ctypes.byref(rows), ctypes.byref(re)),
+           "ifdk_packed_size")
+    return int(vb.value), int(rows.value), int(re.value)
+
+
+def ifdk_pack_views(plan: int, Q, q_dtype: int, view_count: int, Qp, stream=None) -> None:
+    _check(load_library().ifdk_pack_views(plan, _addr(Q), int(q_dtype), int(view_count), _addr(Qp), _stream(stream)),
+           "ifdk_pack_views")
+
+
+def ifdk_backproject_packed(plan: int, Qp, q_dtype: int, view_begin: int, view_count: int, vol,
+                            stream=None) -> None:
+    _check(load_library().ifdk_backproject_packed(plan, _addr(Qp), int(q_dtype), int(view_begin), int(view_count),
+                                                  _addr(vol), _stream(stream)), "ifdk_backproject_packed")
+
+
+def ifdk_set_view_pairing(plan: int, enable: bool) -> None:
+    _check(load_library().ifdk_set_view_pairing(plan, 1 if enable else 0), "ifdk_set_view_pairing")
+
+
+_PACKED_KEYS = ("path", "box_w", "box_h", "z_per_thread", "stages", "smem_bytes", "blocks", "fold_w", "align",
+                "rows", "row_elems", "row0")
+
+
+def ifdk_backproject_packed_info(plan: int, q_dtype: int) -> dict:
+    arr = (ctypes.c_int64 * 12)()
+    _check(load_library().ifdk_backproject_packed_info(plan, int(q_dtype), arr), "ifdk_backproject_packed_info")
+    return dict(zip(_PACKED_KEYS, (int(v) for v in arr)))
+
+
+def ifdk_query_packed(geom: Geometry, q_dtype: int, view_pairing: bool = True) -> dict:
+    """Host-only: the packed launch ifdk_backproject_packed would choose."""
+    h = _GeomHolder(geom)
+    arr = (ctypes.c_int64 * 12)()
+    _check(load_library().ifdk_query_packed(ctypes.byref(h.c), int(q_dtype), 1 if view_pairing else 0, arr),
+           "ifdk_query_packed")
+    return dict(zip(_PACKED_KEYS, (int(v) for v in arr)))
 
 
 def ifdk_project(plan: int, vol, P, view_begin: int, view_count: int, stream=None) -> None:
@@ -335,27 +387,84 @@ class Plan:
         ifdk_backproject_views(self.handle, Qv, dtype_code(Qv.dtype), view_begin, Qv.shape[0], vol, stream)
         return vol
 
+    def staging_elems(self, dtype, chunk_views: int, packed: bool = True) -> int:
+        """Elements of Q_host's dtype the streaming call needs: the two copy halves,
+        plus the two packed halves when the packed path is used."""
+        g = self.geom
+        n = 2 * chunk_views * g.nv * g.nu
+        if packed:
+            try:
+                vb, _, _ = ifdk_packed_size(self.handle, dtype_code(dtype))
+            except IfdkError:
+                vb = 0
+            n += 2 * chunk_views * vb // _ELEM[dtype_code(dtype)]
+        return n
+
     def backproject_host(self, Q_host, vol, staging=None, chunk_views: int = 64, host_row0: int = 0,
-                         view_begin: int = 0, view_count: int | None = None, stream=None):
+                         view_begin: int = 0, view_count: int | None = None, stream=None, packed: bool = True):
         """Back-project views streamed from a (pinned) CPU tensor [np][host_nv][nu]
         whose rows [host_row0, host_row0 + nv) are this plan's detector.
-        staging: device buffer of >= 2 * chunk_views * nv * nu elements of
-        Q_host's dtype (allocated here if None).  Asynchronous on `stream`."""
+        staging: device buffer of Q_host's dtype (allocated here if None) of
+        staging_elems() elements for the packed path (packed=True, when the
+        plan has packed views) or 2 * chunk_views * nv * nu for the direct path.
+        Asynchronous on `stream`."""
         import torch
         g = self.geom
         if (Q_host.is_cuda or not Q_host.is_contiguous() or Q_host.dim() != 3
                 or Q_host.shape[0] != g.np or Q_host.shape[2] != g.nu):
             raise ValueError(f"Q_host must be a contiguous CPU tensor of shape ({g.np}, host_nv, {g.nu})")
         self._check_vol(vol)
-        n = 2 * chunk_views * g.nv * g.nu
+        n = self.staging_elems(Q_host.dtype, chunk_views, packed)
         if staging is None:
             staging = torch.empty(n, dtype=Q_host.dtype, device=vol.device)
-        if staging.dtype != Q_host.dtype or staging.numel() < n or not staging.is_cuda:
+        if staging.dtype != Q_host.dtype or staging.numel() < 2 * chunk_views * g.nv * g.nu or not staging.is_cuda:
             raise ValueError("staging must be a CUDA tensor of Q_host's dtype with >= 2 * chunk_views * nv * nu elements")
         vc = g.np - view_begin if view_count is None else view_count
         ifdk_backproject_host(self.handle, Q_host, dtype_code(Q_host.dtype), Q_host.shape[1], host_row0, view_begin,
                               vc, chunk_views, staging, staging.numel() * staging.element_size(), vol, stream)
         return vol
+
+    def packed_shape(self, dtype):
+        """Shape (np, rows, row_elems, 4) of the packed views for storage dtype."""
+        _, rows, re = ifdk_packed_size(self.handle, dtype_code(dtype))
+        return (self.geom.np, rows, re, 4)
+
+    def pack(self, Q, Qp=None, stream=None):
+        """Packed views of Q (ifdk_pack_views): element (r, c) = Q[r][c], Q[2vc-r][c], Q[r][c+1], Q[2vc-r][c+1]."""
+        import torch
+        if not Q.is_cuda or not Q.is_contiguous() or Q.dim() != 3 or tuple(Q.shape[1:]) != (self.geom.nv, self.geom.nu):
+            raise ValueError(f"Q must be a contiguous CUDA tensor of shape (views, {self.geom.nv}, {self.geom.nu})")
+        shape = (Q.shape[0],) + self.packed_shape(Q.dtype)[1:]
+        if Qp is None:
+            Qp = torch.empty(shape, dtype=Q.dtype, device=Q.device)
+        if not Qp.is_cuda or not Qp.is_contiguous() or tuple(Qp.shape) != shape or Qp.dtype != Q.dtype:
+            raise ValueError(f"Qp must be a contiguous CUDA tensor of shape {shape} and Q's dtype")
+        ifdk_pack_views(self.handle, Q, dtype_code(Q.dtype), Q.shape[0], Qp, stream)
+        return Qp
+
+    def backproject_packed(self, Qp, vol=None, view_begin: int = 0, view_count: int | None = None, stream=None):
+        """Back-projection from packed views of all np views (ifdk_backproject_packed)."""
+        import torch
+        g = self.geom
+        if not Qp.is_cuda or not Qp.is_contiguous() or tuple(Qp.shape) != self.packed_shape(Qp.dtype):
+            raise ValueError(f"Qp must be a contiguous CUDA tensor of shape {self.packed_shape(Qp.dtype)}")
+        if vol is None:
+            vol = torch.zeros((g.nx, g.ny, g.nz), dtype=torch.float32, device=Qp.device)
+        self._check_vol(vol)
+        n = g.np - view_begin if view_count is None else view_count
+        ifdk_backproject_packed(self.handle, Qp, dtype_code(Qp.dtype), view_begin, n, vol, stream)
+        return vol
+
+    def set_view_pairing(self, enable: bool) -> None:
+        """Half-turn view pairing of the packed back-projection (on by default)."""
+        ifdk_set_view_pairing(self.handle, enable)
+
+    def packed_info(self, dtype) -> dict:
+        return ifdk_backproject_packed_info(self.handle, dtype_code(dtype))
+
+    def has_packed(self, dtype) -> bool:
+        """Whether packed views (and ifdk_backproject_packed) serve this geometry."""
+        return self.packed_info(dtype)["path"] > 0
 
     def project(self, vol, P=None, view_begin: int = 0, view_count: int | None = None, stream=None):
         import torch

@@ -22,7 +22,7 @@ PHANTOM_LIB = os.path.join(LIBDIR, "libifdk_phantom.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
            "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
-LIB_SOURCES = ["ifdk_plan.cu", "ifdk_bp.cu", "ifdk_filter.cu", "ifdk_filter_tc.cu", "ifdk_filter_static.cu",
+LIB_SOURCES = ["ifdk_plan.cu", "ifdk_bp.cu", "ifdk_bp_packed.cu", "ifdk_filter.cu", "ifdk_filter_tc.cu", "ifdk_filter_static.cu",
                "ifdk_project.cu", "ifdk_stream.cu"]
 PHANTOM_SOURCES = [os.path.join(PKG, "phantom", "phantom.cu")]
 

@@ -1,0 +1,701 @@
+// Back-projection (Algorithm 4 of the iFDK paper) from packed views, sm_103a.
+//
+// Packed views.  For a volume centred on the source plane with 2 v_c
+// integral, voxel k and its mirror nz-1-k read detector rows that are mirror
+// images about v_c (Theorem 1: v_mirror = 2 v_c - v).  A packed view stores
+// for row r in [r0, floor(v_c) + 3), r0 = min(0, 2 v_c - (nv - 1)) (rows
+// whose mirror lies on the detector), and column c in [-1, nu) the element
+//   (Q[r][c], Q[2vc-r][c], Q[r][c+1], Q[2vc-r][c+1])
+// (zero where a row or column lies outside the detector; column -1 carries
+// the first column as its right tap), so one shared-memory
+// load gives both voxels of a pair the two taps of a detector row.  Packing
+// is one pass over Q (ifdk_pack_views); the back-projection then stages
+// windows of packed views with TMA and uses them as they land.
+//
+// Kernel:
+//   * a block owns a 16 x 16 tile of (i, j) columns and L z pairs
+//     (k, nz-1-k); each thread owns one column and its z-run of pairs;
+//   * per (column, view) a thread forms z, f = 1/z, u, W_dis = w f^2 and the
+//     row slope once (Algorithm 4, Theorems 2 and 3) and reuses them over its
+//     z-run; the pair (k, nz-1-k) shares u, f, W_dis and the row fraction;
+//   * half-turn view pairs (NV = 2): when view s + P (P = np/2) is view s
+//     turned by pi, voxel (X, Y, Z) in view s and voxel (-X, -Y, Z) in view
+//     s + P have the same (u, v, z).  A thread owns column (i, j), j < ny/2,
+//     and the opposite column (nx-1-i, ny-1-j).  Its coordinates in view s
+//     serve its column with view s and the opposite column with view s + P;
+//     its coordinates in view s + P serve its column with view s + P and the
+//     opposite column with view s.  So each pair of views is two view groups,
+//     and each evaluation of the coordinates, the row index and the row
+//     fraction serves four voxel updates;
+//   * a view group's window (the tile's detector footprint in the group's
+//     own view, rows [v0, v0+H)) is one TMA box of the packed views s and
+//     s + P together (a 4-D tensor map whose second dimension steps from view
+//     s to view s + P), so the two views' elements of a row sit side by side;
+//     TMA's zero fill implements "taps outside the detector read 0";
+//   * a ring of stages (one group each) paced by mbarriers: full = the box
+//     landed, empty = every warp finished the group; warp 0 refills the
+//     stage released two groups earlier, so up to stages - 1 groups are in
+//     flight and warps never meet at a block-wide barrier;
+//   * consecutive pairs step about one detector row (the magnification), so
+//     when every lane of a warp steps less than a row, a pair loads only its
+//     upper row and takes the lower one from the previous pair;
+//   * FP32 accumulation in registers over all views, one read-modify-write of
+//     each thread's z-runs at the end (vectorised, 64-bit offsets, k-major).
+//   FP32 / BF16 storage: taps are interpolated in packed f32x2 arithmetic
+//   (BF16 widened by a shift first); FP16 storage: both lerps in packed half2,
+//   widened once before the FP32 accumulate.
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+#include "ifdk_device.cuh"
+#include "ifdk_internal.h"
+
+namespace ifdk {
+namespace {
+
+constexpr int kPkMargin = 1;   // window margin (pixels) on every side
+
+struct PkGeom {              // per stage: the group's window and terms (64 bytes)
+    float A0, A1, A3, B2;    // own view's projection terms (Eq. 2, re-centred)
+    float B3, C0, C1, C3;
+    float w0, uc_l, vc_l, w1;   // FDK weights of the box's view 0 / view 1; window-relative principal point
+    int u0a, v0, pad0, pad1;    // box origin: column (element), row
+};
+
+struct PkArgs {
+    float *vol;
+    const ViewTerms *terms;
+    unsigned int *status;
+    unsigned long long wait_ns;
+    int nx, ny, nz, tiles_x, ny_cols;   // ny_cols: rows j the grid covers (ny, or ny / 2 with NV = 2)
+    int view_begin, view_count;         // NV = 1: views; NV = 2: pairs (s, s + P), s from view_begin
+    int q_view0, q_pair_off;            // view s is packed view s - q_view0 (its partner + q_pair_off)
+    int pair_view_off;                  // P
+    int box_h, stages, row0;            // row0: detector row of packed row 0
+    float cx, cy, cz, uc, vc;
+    uint32_t stage_bytes, box_tx_bytes;
+};
+
+template <typename T> struct PkT;
+template <> struct PkT<float> {
+    static constexpr int ALIGN = 1;
+    static constexpr CUtensorMapDataType TMA = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+};
+template <> struct PkT<__half> {
+    static constexpr int ALIGN = 2;
+    static constexpr CUtensorMapDataType TMA = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+};
+template <> struct PkT<__nv_bfloat16> {
+    static constexpr int ALIGN = 2;
+    static constexpr CUtensorMapDataType TMA = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+};
+
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+__device__ __forceinline__ void sts_f32x4(uint32_t a, float4 v)
+{
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ void sts_i32x4(uint32_t a, int4 v)
+{
+    asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t lds_u32_v(uint32_t a)
+{
+    uint32_t r;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r) : "r"(a));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Orders this thread's earlier generic-proxy shared-memory accesses (and those
+// it synchronised with) before its later async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bounded wait for phase `parity`: spins on try_wait (which suspends the warp
+// for a while in hardware) and reads the clock only every 16 tries.
+__device__ __forceinline__ bool mbar_wait_lim(uint32_t bar, uint32_t parity, unsigned long long limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15u) == 0 && global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+// Packed FP32 lerp(a, b, t) = a + t (b - a), each step rounded once.
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float2 t)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    return __ffma2_rn(t, __ffma2_rn(a, m1, b), a);
+}
+
+// 1/z for z > 0 (here z >= 0.1 d): hardware approximation refined by one
+// Newton-Raphson step r (2 - z r), within an ulp or so of the rounded quotient.
+__device__ __forceinline__ float rcp_nr(float z)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(z));
+    return r * fmaf(-z, r, 2.0f);
+}
+
+// Storage-type specific parts: element size, the u-interpolated (direct,
+// mirror) row of an element and the v-lerp + weighted accumulate of a pair.
+template <typename T> struct Tap;
+template <> struct Tap<float> {
+    static constexpr uint32_t ES = 16;
+    using R = float2;
+    __device__ __forceinline__ static R row(const unsigned char *e, float2 du2, __half2)
+    {
+        const float4 q = *reinterpret_cast<const float4 *>(e);
+        return lerp2(make_float2(q.x, q.y), make_float2(q.z, q.w), du2);
+    }
+    __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2 dv2, __half2, float2 W2)
+    {
+        return __ffma2_rn(W2, lerp2(lo, hi, dv2), acc);
+    }
+};
+template <> struct Tap<__half> {
+    static constexpr uint32_t ES = 8;
+    using R = __half2;
+    __device__ __forceinline__ static R row(const unsigned char *e, float2, __half2 duh)
+    {
+        const uint2 q = *reinterpret_cast<const uint2 *>(e);
+        const __half2 hx = *reinterpret_cast<const __half2 *>(&q.x), hy = *reinterpret_cast<const __half2 *>(&q.y);
+        return __hfma2(duh, __hsub2(hy, hx), hx);
+    }
+    __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2, __half2 dvh, float2 W2)
+    {
+        return __ffma2_rn(W2, __half22float2(__hfma2(dvh, __hsub2(hi, lo), lo)), acc);
+    }
+};
+template <> struct Tap<__nv_bfloat16> {
+    static constexpr uint32_t ES = 8;
+    using R = float2;
+    __device__ __forceinline__ static R row(const unsigned char *e, float2 du2, __half2)
+    {
+        const uint2 q = *reinterpret_cast<const uint2 *>(e);
+        return lerp2(make_float2(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xffff0000u)),
+                     make_float2(__uint_as_float(q.y << 16), __uint_as_float(q.y & 0xffff0000u)), du2);
+    }
+    __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2 dv2, __half2, float2 W2)
+    {
+        return __ffma2_rn(W2, lerp2(lo, hi, dv2), acc);
+    }
+};
+
+// The z-run of one (column, view group): pair p samples box rows n_p, n_p + 1
+// at v_p = vb + p sig (window coordinates).  The box holds NV views side by
+// side in each row (HB bytes apart, rows ROWB bytes apart); view 0's taps go
+// to a0 with weight W0, view 1's to a1 with weight W1.  With REUSE (every
+// lane of the warp has sig < 1, so n_{p+1} - n_p is 0 or 1) a pair loads only
+// row n_p + 1 and takes row n_p from the previous pair's upper row when it
+// moved up; otherwise it loads both rows.
+template <typename T, int NV, int L, uint32_t ROWB, uint32_t HB, bool REUSE>
+__device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], const unsigned char *sm,
+                                          uint32_t base, float sig, float vb, float2 du2, __half2 duh, float2 W0,
+                                          float2 W1)
+{
+    using R = typename Tap<T>::R;
+    R lo[NV], hi[NV];
+    float dv;
+    uint32_t tv = floor_frac(vb, dv);
+    const unsigned char *e = sm + (base + tv * ROWB);   // 32-bit offset arithmetic wraps the biases away
+#pragma unroll
+    for (int n = 0; n < NV; ++n) {
+        lo[n] = Tap<T>::row(e + n * HB, du2, duh);
+        hi[n] = Tap<T>::row(e + ROWB + n * HB, du2, duh);
+    }
+    a0[0] = Tap<T>::accum(a0[0], lo[0], hi[0], make_float2(dv, dv), __float2half2_rn(dv), W0);
+    if constexpr (NV == 2) a1[0] = Tap<T>::accum(a1[0], lo[1], hi[1], make_float2(dv, dv), __float2half2_rn(dv), W1);
+#pragma unroll
+    for (int p = 1; p < L; ++p) {
+        const uint32_t tn = floor_frac(fmaf((float)p, sig, vb), dv);
+        e = sm + (base + tn * ROWB);
+        const float2 dv2 = make_float2(dv, dv);
+        const __half2 dvh = __float2half2_rn(dv);
+        if constexpr (REUSE) {
+            const bool moved = tn != tv;
+            tv = tn;
+#pragma unroll
+            for (int n = 0; n < NV; ++n) {
+                const R hn = Tap<T>::row(e + ROWB + n * HB, du2, duh);
+                lo[n] = moved ? hi[n] : lo[n];
+                hi[n] = hn;
+            }
+        } else {
+#pragma unroll
+            for (int n = 0; n < NV; ++n) {
+                lo[n] = Tap<T>::row(e + n * HB, du2, duh);
+                hi[n] = Tap<T>::row(e + ROWB + n * HB, du2, duh);
+            }
+        }
+        a0[p] = Tap<T>::accum(a0[p], lo[0], hi[0], dv2, dvh, W0);
+        if constexpr (NV == 2) a1[p] = Tap<T>::accum(a1[p], lo[1], hi[1], dv2, dvh, W1);
+    }
+}
+
+// Writes a z-run: acc[p].x -> voxel k0+p, acc[p].y -> its mirror nz-1-k0-p, of column (i, j).
+template <int L>
+__device__ __forceinline__ void write_run(const PkArgs &a, int k0, int i, int j, const float2 *acc)
+{
+    float *col = a.vol + ((size_t)i * a.ny + j) * (size_t)a.nz;
+    const int half = a.nz / 2, npairs = (a.nz + 1) / 2;
+    if ((a.nz & 3) == 0 && k0 + L <= half) {
+        float4 *pd = reinterpret_cast<float4 *>(col + k0);
+        float4 *pm = reinterpret_cast<float4 *>(col + (a.nz - k0 - L));
+#pragma unroll
+        for (int q = 0; q < L / 4; ++q) {
+            float4 d = pd[q];
+            d.x += acc[4 * q].x; d.y += acc[4 * q + 1].x; d.z += acc[4 * q + 2].x; d.w += acc[4 * q + 3].x;
+            pd[q] = d;
+            float4 m = pm[q];   // voxels nz-k0-L+4q .. +3 mirror pairs L-1-4q .. L-4-4q
+            m.x += acc[L - 1 - 4 * q].y; m.y += acc[L - 2 - 4 * q].y;
+            m.z += acc[L - 3 - 4 * q].y; m.w += acc[L - 4 - 4 * q].y;
+            pm[q] = m;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < L; ++p) {
+            const int k = k0 + p;
+            if (k < npairs) {
+                col[k] += acc[p].x;
+                const int km = a.nz - 1 - k;
+                if (km > k) col[km] += acc[p].y;
+            }
+        }
+    }
+}
+
+// Shared-memory map (offsets from a 128-byte aligned base): full barriers at
+// 8 s, empty barriers at 64 + 8 s, the abort flag at 128, stages from 256;
+// a stage is its PkGeom (128 bytes reserved) followed by the box.
+constexpr uint32_t kPkFull = 0, kPkEmpty = 64, kPkAbort = 128, kPkStage0 = 256, kPkBox = 128;
+static_assert(kPkMaxStages * 8 <= 64, "barrier map");
+
+template <typename T, int NV, int BW, int L>
+__global__ void __launch_bounds__(kThreads, NV == 1 ? 3 : 2)
+    bp_packed_kernel(const PkArgs a, const __grid_constant__ CUtensorMap tmap)
+{
+    constexpr uint32_t ES = Tap<T>::ES;
+    constexpr int ALIGN = PkT<T>::ALIGN;
+    constexpr uint32_t HB = BW * ES;       // one view's part of a box row, bytes
+    constexpr uint32_t ROWB = NV * HB;     // box row, bytes
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    const uint32_t sbase = smem_addr(smem_dyn);
+    const uint32_t pad = (128u - (sbase & 127u)) & 127u;
+    const uint32_t s0 = sbase + pad;                 // shared-window address of the map
+    const unsigned char *sm = smem_dyn + pad;        // the same, as a pointer
+    const int S = a.stages;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // block coordinates: warp = 16 x 2 patch of columns, 8 warps per 16 x 16 tile
+    const int i0 = (blockIdx.x % a.tiles_x) * kTileX, j0 = (blockIdx.x / a.tiles_x) * kTileY;
+    const int k0 = blockIdx.y * L;
+    const int ci = i0 + (lane & 15), cj = j0 + warp * 2 + (lane >> 4);
+    const float ip = (float)ci - a.cx, jp = (float)cj - a.cy, kp0 = (float)k0 - a.cz;
+
+    if (tid == 0) {
+        // a bounded wait of this plan ran out (and was not read yet): the
+        // results are void, so blocks that start after it do no work
+        sts_u32(s0 + kPkAbort, *reinterpret_cast<volatile const unsigned int *>(a.status) & kStatusTimeout);
+        prefetch_tmap(&tmap);
+        for (int st = 0; st < S; ++st) {
+            mbar_init(s0 + kPkFull + 8 * st, 1);
+            mbar_init(s0 + kPkEmpty + 8 * st, kThreads / 32);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (lds_u32_v(s0 + kPkAbort) != 0) return;
+
+    const int ngroups = NV * a.view_count;
+    // Lane 0 of warp 0: window of group t (own view's footprint of the tile),
+    // its terms and the TMA box into stage t % S.
+    auto issue = [&](int t) {
+        const int st = t % S;
+        const uint32_t sg = s0 + kPkStage0 + (uint32_t)st * a.stage_bytes;
+        const int s = a.view_begin + (NV == 2 ? (t >> 1) : t);    // view 0 of the box
+        const int own = s + (NV == 2 ? (t & 1) * a.pair_view_off : 0);
+        const float4 *tp = reinterpret_cast<const float4 *>(a.terms + own);
+        const float4 t0 = __ldg(tp), t1 = __ldg(tp + 1);
+        const float w0 = __ldg(&a.terms[s].w);
+        const float w1 = NV == 2 ? __ldg(&a.terms[s + a.pair_view_off].w) : 0.0f;
+        // t0 = (A0, A1, A3, B2), t1 = (B3, C0, C1, C3)
+        const float ia = (float)i0 - a.cx, ib = ia + (kTileX - 1);
+        const float ja = (float)j0 - a.cy, jb = ja + (kTileY - 1);
+        float zc[4], uq[4];
+        const float cx4[4] = {ia, ib, ia, ib}, cy4[4] = {ja, ja, jb, jb};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            zc[q] = fmaf(t1.y, cx4[q], fmaf(t1.z, cy4[q], t1.w));
+            uq[q] = fmaf(t0.x, cx4[q], fmaf(t0.y, cy4[q], t0.z)) / zc[q];
+        }
+        const float u_lo = fminf(fminf(uq[0], uq[1]), fminf(uq[2], uq[3]));
+        const float z_lo = fminf(fminf(zc[0], zc[1]), fminf(zc[2], zc[3]));
+        const float z_hi = fmaxf(fmaxf(zc[0], zc[1]), fmaxf(zc[2], zc[3]));
+        const float e0 = fmaf(t0.w, kp0, t1.x), e1 = fmaf(t0.w, kp0 + (L - 1), t1.x);
+        const float v_lo = fminf(fminf(e0 / z_lo, e0 / z_hi), fminf(e1 / z_lo, e1 / z_hi));
+        // box from column u0a (element u0a + 1): TMA needs the element index times
+        // its 4 * sizeof(T) bytes on a 16-byte boundary, so u0a + 1 is a multiple of ALIGN
+        const int u0a = floor_div((int)floorf(a.uc + u_lo) - kPkMargin + 1, ALIGN) * ALIGN - 1;
+        const int v0 = (int)floorf(a.vc + v_lo) - kPkMargin;
+        sts_f32x4(sg, t0);
+        sts_f32x4(sg + 16, t1);
+        sts_f32x4(sg + 32, make_float4(w0, a.uc - (float)u0a, a.vc - (float)v0, w1));
+        const uint32_t bar = s0 + kPkFull + 8u * st;
+        fence_proxy_async_shared();
+        mbar_arrive_expect_tx(bar, a.box_tx_bytes);
+        const int q = s - a.q_view0;
+        if constexpr (NV == 2)
+            tma_load_4d(sg + kPkBox, &tmap, 4 * (u0a + 1), 0, v0 - a.row0, q, bar);
+        else
+            tma_load_3d(sg + kPkBox, &tmap, 4 * (u0a + 1), v0 - a.row0, q, bar);
+    };
+
+    int issued = min(S, ngroups);   // groups issued so far (tracked by warp 0)
+    if (warp == 0 && lane == 0)
+        for (int t = 0; t < issued; ++t) issue(t);
+
+    float2 acc[NV][L];
+#pragma unroll
+    for (int n = 0; n < NV; ++n)
+#pragma unroll
+        for (int p = 0; p < L; ++p) acc[n][p] = make_float2(0.0f, 0.0f);
+
+    // One view group t: wait for its box, form the column terms, run the z-run.
+    // SWAP (the second group of a half-turn pair): the box's view 0 (view s)
+    // feeds the opposite column and view 1 (view s + P) this thread's column.
+    bool ok = true;
+    auto group = [&](int t, auto swap_tag) {
+        constexpr bool SWAP = decltype(swap_tag)::value;
+        const int st = t % S;
+        const uint32_t parity = (uint32_t)(t / S) & 1u;
+        // refill the stage group t - 2 used (every warp finished it by now, or soon)
+        if (warp == 0 && t >= 2 && issued < ngroups) {
+            bool e = true;
+            if (lane == 0) {
+                e = mbar_wait_lim(s0 + kPkEmpty + 8u * ((t - 2) % S), (uint32_t)((t - 2) / S) & 1u, a.wait_ns);
+                if (e) issue(issued);
+            }
+            ok = __shfl_sync(0xffffffffu, e, 0) != 0;
+            ++issued;
+            if (!ok) return;
+        }
+        ok = __all_sync(0xffffffffu, mbar_wait_lim(s0 + kPkFull + 8u * st, parity, a.wait_ns));
+        if (!ok) return;
+        const uint32_t sg = kPkStage0 + (uint32_t)st * a.stage_bytes;
+        const float4 *gp = reinterpret_cast<const float4 *>(sm + sg);
+        const float4 t0 = gp[0], t1 = gp[1], t2 = gp[2];
+        // Theorems 2 and 3: z, u and W_dis do not depend on k
+        const float z = fmaf(t1.y, ip, fmaf(t1.z, jp, t1.w));
+        const float f = rcp_nr(z);
+        const float x = fmaf(t0.x, ip, fmaf(t0.y, jp, t0.z));
+        float du;
+        const uint32_t tu = floor_frac(fmaf(x, f, t2.y), du);
+        const float ff = f * f;
+        const float2 W0 = make_float2(t2.x * ff, t2.x * ff), W1 = make_float2(t2.w * ff, t2.w * ff);
+        const float sig = t0.w * f;
+        const float vb = fmaf(sig, kp0, fmaf(t1.x, f, t2.z));
+        // element (n, cu) at offset base + bits(t_v) * ROWB (mod 2^32): n = bits(t_v) - bias,
+        // cu = bits(t_u) - bias
+        const uint32_t base = sg + kPkBox + (tu - kFloorBias) * ES - kFloorBias * ROWB;
+        const float2 du2 = make_float2(du, du);
+        const __half2 duh = __float2half2_rn(du);
+        float2(&c0)[L] = SWAP ? acc[NV - 1] : acc[0];
+        float2(&c1)[L] = SWAP ? acc[0] : acc[NV - 1];
+        // sig < 1 - 2^-10 keeps fp32 rounding of v_{p+1} - v_p below one row
+        if (__all_sync(0xffffffffu, sig < 0.9990234375f))
+            pair_loop<T, NV, L, ROWB, HB, true>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1);
+        else
+            pair_loop<T, NV, L, ROWB, HB, false>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(s0 + kPkEmpty + 8u * st);
+    };
+    if constexpr (NV == 2) {
+        for (int t = 0; ok && t < ngroups; t += 2) {
+            group(t, std::false_type{});
+            if (ok) group(t + 1, std::true_type{});
+        }
+    } else {
+        for (int t = 0; ok && t < ngroups; ++t) group(t, std::false_type{});
+    }
+    if (!ok) {
+        // record the timeout; warp 0 keeps shared memory alive until every box it
+        // issued has landed (a stage holds at most one box in flight)
+        if (lane == 0) atomicOr(a.status, kStatusTimeout);
+        if (warp == 0 && lane == 0)
+            for (int t = max(0, issued - S); t < issued; ++t)
+                mbar_wait_lim(s0 + kPkFull + 8u * (t % S), (uint32_t)(t / S) & 1u, a.wait_ns);
+        return;
+    }
+    if (ci < a.nx && cj < a.ny_cols) {
+        write_run<L>(a, k0, ci, cj, acc[0]);
+        if constexpr (NV == 2) write_run<L>(a, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
+    }
+}
+
+// Packing: element e of row r of view s, column c = e - 1:
+// (Q[r][c], Q[2vc-r][c], Q[r][c+1], Q[2vc-r][c+1]).
+__device__ __forceinline__ uint32_t bits16(__half x) { return __half_as_ushort(x); }
+__device__ __forceinline__ uint32_t bits16(__nv_bfloat16 x) { return __bfloat16_as_ushort(x); }
+__device__ __forceinline__ uint32_t bits16(float) { return 0u; }
+struct PackArgs {
+    long long n_elems;   // n_views * rows * nu_p
+    int nv, nu, nu_p, rows, row0, two_vc;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) pack_kernel(const T *__restrict__ Q, T *__restrict__ P, const PackArgs a)
+{
+    const T zero = T(0.0f);
+    for (long long e = blockIdx.x * 256ll + threadIdx.x; e < a.n_elems; e += (long long)gridDim.x * 256) {
+        const int c = (int)(e % a.nu_p) - 1;
+        const long long sr = e / a.nu_p;
+        const int r = (int)(sr % a.rows) + a.row0;
+        const long long s = sr / a.rows;
+        const T *qv = Q + s * a.nv * (long long)a.nu;
+        const int rm = a.two_vc - r;
+        const bool dr = r >= 0 && r < a.nv, mr = rm >= 0 && rm < a.nv;
+        const bool c0 = c >= 0 && c < a.nu, c1 = c + 1 < a.nu;   // c + 1 >= 0 always
+        const T v0 = dr && c0 ? qv[(long long)r * a.nu + c] : zero;
+        const T v1 = mr && c0 ? qv[(long long)rm * a.nu + c] : zero;
+        const T v2 = dr && c1 ? qv[(long long)r * a.nu + c + 1] : zero;
+        const T v3 = mr && c1 ? qv[(long long)rm * a.nu + c + 1] : zero;
+        T *d = P + e * 4;
+        if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float4 *>(d) = make_float4(v0, v1, v2, v3);
+        } else {
+            *reinterpret_cast<uint2 *>(d) = make_uint2(bits16(v0) | (bits16(v1) << 16), bits16(v2) | (bits16(v3) << 16));
+        }
+    }
+}
+
+// Host sizing of the packed kernel: windows from analytic FP64 bounds of the
+// largest detector footprint of any block over any view.
+PkLaunch size_packed(const ifdk_plan_s *p, int q_dtype, int nv)
+{
+    const ifdk_geometry &g = p->g;
+    PkLaunch b{};
+    b.path = 0;
+    b.nv = nv;
+    const int es = (int)dtype_size(q_dtype);
+    b.align = q_dtype == IFDK_F32 ? 1 : 2;
+    const int ny_cols = nv == 2 ? g.ny / 2 : g.ny;
+    const int tiles_x = (g.nx + kTileX - 1) / kTileX, tiles_y = (ny_cols + kTileY - 1) / kTileY;
+    const int L = pk_pairs(nv), npairs = (g.nz + 1) / 2, zblocks = (npairs + L - 1) / L;
+    b.grid_x = tiles_x * tiles_y;
+    b.grid_y = zblocks;
+    if (!p->fold_ok) return b;
+    if (nv == 2 && (!p->half_turn || g.ny % 2 != 0)) return b;
+    const double cx = (g.nx - 1) / 2.0, cy = (g.ny - 1) / 2.0, cz = (g.nz - 1) / 2.0;
+    const double xa = cx * g.dx, xb = (tiles_x * kTileX - 1 - cx) * g.dx;
+    const double ya = cy * g.dy, yb = (tiles_y * kTileY - 1 - cy) * g.dy;
+    const double rxy = std::sqrt(std::max(xa * xa, xb * xb) + std::max(ya * ya, yb * yb));
+    const double cmin = g.sid - rxy;
+    if (cmin < 0.1 * g.sid) return b;
+    const double et = std::hypot((kTileX - 1) * g.dx, (kTileY - 1) * g.dy);
+    const double wu = g.sdd / g.du * et * (1.0 / cmin + 2.0 * rxy / (cmin * cmin));
+    const double kmax = std::max(cz, (double)zblocks * L - 1 - cz);
+    const double b2 = g.sdd * g.dz / g.dv;
+    const double hv = b2 * (L - 1) / cmin + b2 * kmax * et / (cmin * cmin);
+    b.fold_w = (int)std::ceil(wu) + 2 * kPkMargin + 2;
+    b.box_h = (int)std::ceil(hv) + 2 * kPkMargin + 3;
+    const int need = b.fold_w + b.align - 1;   // the window starts up to align - 1 into the box
+    b.bw = need <= kPkBoxS ? kPkBoxS : kPkBoxL;
+    if (need > kPkBoxL || b.box_h > 256) return b;
+    const size_t box = (size_t)b.box_h * nv * b.bw * 4 * es;
+    b.stage_bytes = (kPkBox + box + 127) / 128 * 128;
+    // as many stages as keep 3 (nv = 1) or 2 (nv = 2) blocks per SM, at most 8
+    const size_t budget = nv == 1 ? 74 * 1024 : 112 * 1024;
+    b.stages = (int)std::min<size_t>(kPkMaxStages, (budget - 128 - kPkStage0) / b.stage_bytes);
+    if (b.stages < 3) b.stages = 3;   // fewer blocks per SM rather than a shallower ring
+    b.smem = 128 + kPkStage0 + (size_t)b.stages * b.stage_bytes;
+    if (b.smem > 220 * 1024) return b;
+    if ((size_t)g.np * p->pk_rows * p->pk_nu * 4 * es >= ((size_t)1 << 40) || zblocks > 65535) return b;
+    b.pairs = L;
+    b.path = 1;
+    return b;
+}
+
+template <typename T, int NV, int BW>
+int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_begin, int s_count, int q_view0,
+                    int q_pair_off, int q_views, float *vol, cudaStream_t stream)
+{
+    const ifdk_geometry &g = p->g;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return IFDK_ERR_CUDA;
+    const cuuint64_t es = sizeof(T);
+    const cuuint64_t row_bytes = (cuuint64_t)p->pk_nu * 4 * es, view_bytes = row_bytes * p->pk_rows;
+    CUtensorMap tmap;
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r;
+    if (NV == 2) {
+        // x (elements), view half (view s -> s + P), row, view
+        const cuuint64_t dims[4] = {(cuuint64_t)p->pk_nu * 4, 2, (cuuint64_t)p->pk_rows, (cuuint64_t)q_views};
+        const cuuint64_t strides[3] = {(cuuint64_t)q_pair_off * view_bytes, row_bytes, view_bytes};
+        const cuuint32_t box[4] = {(cuuint32_t)(4 * BW), 2, (cuuint32_t)b.box_h, 1};
+        r = enc(&tmap, PkT<T>::TMA, 4, const_cast<void *>(Qp), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[3] = {(cuuint64_t)p->pk_nu * 4, (cuuint64_t)p->pk_rows, (cuuint64_t)q_views};
+        const cuuint64_t strides[2] = {row_bytes, view_bytes};
+        const cuuint32_t box[3] = {(cuuint32_t)(4 * BW), (cuuint32_t)b.box_h, 1};
+        r = enc(&tmap, PkT<T>::TMA, 3, const_cast<void *>(Qp), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (r != CUDA_SUCCESS) return IFDK_ERR_CUDA;
+    PkArgs a;
+    a.vol = vol;
+    a.terms = p->d_terms;
+    a.status = p->d_status;
+    a.wait_ns = p->wait_ns;
+    a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
+    a.ny_cols = NV == 2 ? g.ny / 2 : g.ny;
+    a.tiles_x = (g.nx + kTileX - 1) / kTileX;
+    a.view_begin = s_begin;
+    a.view_count = s_count;
+    a.q_view0 = q_view0;
+    a.q_pair_off = q_pair_off;
+    a.pair_view_off = g.np / 2;
+    a.box_h = b.box_h;
+    a.stages = b.stages;
+    a.row0 = p->pk_row0;
+    a.cx = (float)((g.nx - 1) / 2.0); a.cy = (float)((g.ny - 1) / 2.0); a.cz = (float)((g.nz - 1) / 2.0);
+    a.uc = (float)p->uc; a.vc = (float)p->vc;
+    a.stage_bytes = (uint32_t)b.stage_bytes;
+    a.box_tx_bytes = (uint32_t)((size_t)b.box_h * NV * BW * 4 * es);
+    void (*kern)(const PkArgs, const CUtensorMap) = bp_packed_kernel<T, NV, BW, pk_pairs(NV)>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem) != cudaSuccess)
+        return IFDK_ERR_CUDA;
+    kern<<<dim3(b.grid_x, b.grid_y), kThreads, b.smem, stream>>>(a, tmap);
+    return cudaGetLastError() == cudaSuccess ? IFDK_OK : IFDK_ERR_CUDA;
+}
+
+template <typename T, int NV>
+int launch_packed_bw(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_begin, int s_count, int q_view0,
+                     int q_pair_off, int q_views, float *vol, cudaStream_t stream)
+{
+    return b.bw == kPkBoxS
+               ? launch_packed_t<T, NV, kPkBoxS>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream)
+               : launch_packed_t<T, NV, kPkBoxL>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream);
+}
+
+template <int NV>
+int launch_packed(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin, int s_count, int q_view0, int q_pair_off,
+                  int q_views, float *vol, cudaStream_t stream)
+{
+    if (s_count <= 0) return IFDK_OK;
+    const PkLaunch &b = NV == 2 ? p->pk2[q_dtype] : p->pk[q_dtype];
+    if (!b.path) return IFDK_ERR_UNSUPPORTED;
+    switch (q_dtype) {
+    case IFDK_F32:
+        return launch_packed_bw<float, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream);
+    case IFDK_F16:
+        return launch_packed_bw<__half, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream);
+    default:
+        return launch_packed_bw<__nv_bfloat16, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol,
+                                                   stream);
+    }
+}
+
+}  // namespace
+
+void split_half_turn(int np, int b, int e, int *m)
+{
+    const int h = np / 2;
+    *m = b;
+    if (np < 2 || np % 2 != 0 || b >= h) return;
+    const int mm = std::min(h, e - h);
+    if (mm > b) *m = mm;
+}
+
+void plan_packed(ifdk_plan_s *p)
+{
+    // rows r0 = min(0, 2 vc - (nv - 1)) .. floor(vc) + 2: every row a voxel
+    // k <= nz / 2 taps (v <= vc, plus FP32 rounding), and rows above the
+    // detector whose mirror lies on it
+    p->pk_row0 = std::min(0, p->two_vc - (p->g.nv - 1));
+    p->pk_rows = p->fold_ok ? (int)std::floor(p->vc) + 3 - p->pk_row0 : 0;
+    p->pk_nu = (p->g.nu + 2) / 2 * 2;   // columns -1 .. nu - 1, rounded up to even
+    for (int t = 0; t < 3; ++t) {
+        p->pk[t] = size_packed(p, t, 1);
+        p->pk2[t] = p->pk[t].path ? size_packed(p, t, 2) : PkLaunch{};
+    }
+}
+
+size_t packed_view_bytes(const ifdk_plan_s *p, int q_dtype)
+{
+    return (size_t)p->pk_rows * p->pk_nu * 4 * dtype_size(q_dtype);
+}
+
+int launch_pack(ifdk_plan_s *p, const void *Q, int q_dtype, int n_views, void *Qp, cudaStream_t stream)
+{
+    if (n_views <= 0) return IFDK_OK;
+    PackArgs a;
+    a.nv = p->g.nv; a.nu = p->g.nu; a.nu_p = p->pk_nu; a.rows = p->pk_rows; a.row0 = p->pk_row0;
+    a.two_vc = p->two_vc;
+    a.n_elems = (long long)n_views * a.rows * a.nu_p;
+    const long long blocks = std::min<long long>((a.n_elems + 255) / 256, 152ll * 64);
+    switch (q_dtype) {
+    case IFDK_F32:
+        pack_kernel<float><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const float *>(Q), static_cast<float *>(Qp), a);
+        break;
+    case IFDK_F16:
+        pack_kernel<__half><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const __half *>(Q), static_cast<__half *>(Qp), a);
+        break;
+    default:
+        pack_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const __nv_bfloat16 *>(Q),
+                                                                       static_cast<__nv_bfloat16 *>(Qp), a);
+    }
+    return cudaGetLastError() == cudaSuccess ? IFDK_OK : IFDK_ERR_CUDA;
+}
+
+int launch_packed_pairs(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin, int s_count, int q_view0,
+                        int q_pair_off, int q_views, float *vol, cudaStream_t stream)
+{
+    return launch_packed<2>(p, Qp, q_dtype, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream);
+}
+
+int launch_backproject_packed(ifdk_plan_s *p, const void *Qp, int q_dtype, int view_begin, int view_count,
+                              int q_view0, int q_views, float *vol, cudaStream_t stream)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return IFDK_ERR_CUDA;
+    const int b = view_begin, e = view_begin + view_count, h = p->g.np / 2;
+    int m = b;
+    if (p->use_half_turn && p->pk2[q_dtype].path) split_half_turn(p->g.np, b, e, &m);
+    if (m == b) return launch_packed<1>(p, Qp, q_dtype, b, view_count, q_view0, 0, q_views, vol, stream);
+    // views s in [b, m) with their partners s + h; then the unpaired [m, b + h) and [m + h, e)
+    int rc = launch_packed<2>(p, Qp, q_dtype, b, m - b, q_view0, h, q_views, vol, stream);
+    if (rc == IFDK_OK) rc = launch_packed<1>(p, Qp, q_dtype, m, b + h - m, q_view0, 0, q_views, vol, stream);
+    if (rc == IFDK_OK) rc = launch_packed<1>(p, Qp, q_dtype, m + h, e - m - h, q_view0, 0, q_views, vol, stream);
+    return rc;
+}
+
+}  // namespace ifdk

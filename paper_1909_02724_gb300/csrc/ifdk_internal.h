@@ -44,6 +44,25 @@ struct BpLaunch {
     int grid_x, grid_y;
 };
 
+// Back-projection from packed (pre-folded) views: block tile as above, a ring
+// of TMA stages of one view group each.
+constexpr int kPkMaxStages = 8;
+constexpr int kPkBoxS = 32, kPkBoxL = 48;   // box widths (elements) the kernel is built for
+// z pairs per thread: 16 for single views, 12 with half-turn view pairs (two columns' runs)
+constexpr int pk_pairs(int nv) { return nv == 2 ? 12 : 16; }
+
+struct PkLaunch {
+    int path;          // 1 = packed mirror-pair kernel applies, 0 = not
+    int nv;            // views per group: 1, or 2 (half-turn view pairs)
+    int fold_w;        // window width (pixels)
+    int bw, box_h;     // TMA box: elements (u), rows
+    int align;         // u alignment of the box start (pixels)
+    int stages;        // TMA stages in the ring
+    int pairs;         // z pairs per thread
+    size_t stage_bytes, smem;
+    int grid_x, grid_y;
+};
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -70,6 +89,12 @@ struct ifdk_plan_s {
     int two_vc = 0;                      // 2 vc when it is an integer
     bool fold_ok = false;                // mirror-pair fold path applicable
     ifdk::BpLaunch bp[3];                // per storage type
+    // packed views: rows r in [pk_row0, pk_row0 + pk_rows) pair row r with row 2 vc - r; a row
+    // holds pk_nu elements (columns -1 .. nu - 1, rounded up to even) of 4 values each
+    int pk_rows = 0, pk_nu = 0, pk_row0 = 0;   // pk_row0: detector row of packed row 0 (<= 0)
+    ifdk::PkLaunch pk[3], pk2[3];        // per storage type: single views / half-turn view pairs
+    bool half_turn = false;              // view s + np/2 is view s turned by pi (exactly)
+    bool use_half_turn = true;           // caller switch (ifdk_set_view_pairing)
     unsigned long long wait_ns = 2000000000ull;
     // tensor-core filter: Toeplitz matrix as 3 BF16 planes [3][tc_npad][tc_kpad]
     int tc_kpad = 0, tc_npad = 0;
@@ -96,6 +121,23 @@ int launch_filter_tc(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int t
 int launch_project(ifdk_plan_s *p, const float *vol, float *P, int view_begin, int view_count,
                    cudaStream_t stream);
 int launch_wait_selftest(ifdk_plan_s *p, unsigned long long ns, cudaStream_t stream);
+// Packed views (ifdk_bp_packed.cu).
+void plan_packed(ifdk_plan_s *p);
+size_t packed_view_bytes(const ifdk_plan_s *p, int q_dtype);
+// Q: [n_views][nv][nu] -> Qp: [n_views][pk_rows][pk_nu][4].
+int launch_pack(ifdk_plan_s *p, const void *Q, int q_dtype, int n_views, void *Qp, cudaStream_t stream);
+// Views [view_begin, view_begin + view_count) from packed views Qp that hold
+// views [q_view0, q_view0 + q_views): half-turn pairs inside the range (if
+// the plan pairs views) are back-projected together, the rest singly.
+int launch_backproject_packed(ifdk_plan_s *p, const void *Qp, int q_dtype, int view_begin, int view_count,
+                              int q_view0, int q_views, float *vol, cudaStream_t stream);
+// Half-turn pairs (s, s + np/2) for s in [s_begin, s_begin + s_count); view s
+// is packed view s - q_view0 and its partner packed view s - q_view0 + q_pair_off.
+int launch_packed_pairs(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin, int s_count, int q_view0,
+                        int q_pair_off, int q_views, float *vol, cudaStream_t stream);
+// The views of [b, e) that pair up: s in [b, *m) with partners in [b + np/2, *m + np/2);
+// the rest are [*m, b + np/2) and [*m + np/2, e).  *m = b when nothing pairs.
+void split_half_turn(int np, int b, int e, int *m);
 int check_backproject_args(const ifdk_plan_s *p, const void *Q, int q_dtype, int view_begin, int view_count,
                            const float *vol);
 }  // namespace ifdk

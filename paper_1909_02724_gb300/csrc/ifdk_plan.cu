@@ -84,6 +84,12 @@ int init_host_plan(ifdk_plan_s *p, const ifdk_geometry *gin)
     const double two_vc = 2.0 * p->vc;
     p->two_vc = (int)std::lround(two_vc);
     p->fold_ok = std::fabs(two_vc - p->two_vc) < 1e-9 && g.vol_off_z == 0.0;
+    // Half-turn view pairs: view s + np/2 is view s turned by pi, so voxel
+    // (X, Y, Z) in view s and (-X, -Y, Z) in view s + np/2 project to the same
+    // (u, v) with the same z (Mrot(b + pi) = -Mrot(b) in the XY plane).
+    p->half_turn = g.np >= 2 && g.np % 2 == 0;
+    for (int s = 0; p->half_turn && s < g.np / 2; ++s)
+        p->half_turn = std::fabs(std::remainder(g.angles[s + g.np / 2] - g.angles[s] - M_PI, 2.0 * M_PI)) < 1e-9;
 
     // Per-view projection terms, FP64 (Eq. 2: M1 . Mrot(b) . M0, multiplied out
     // in closed form and re-centred on the volume centre and principal point).
@@ -203,6 +209,7 @@ int ifdk_create(ifdk_plan *out, const ifdk_geometry *gin)
              cudaEventCreateWithFlags(&p->ev_bp[b], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) { cudaGetLastError(); ifdk_destroy(p); return IFDK_ERR_CUDA; }
     plan_backproject(p);
+    plan_packed(p);
     *out = p;
     return IFDK_OK;
 }
@@ -276,6 +283,46 @@ int ifdk_backproject_views(ifdk_plan p, const void *Qv, int q_dtype, int view_be
                               (cudaStream_t)stream);
 }
 
+int ifdk_packed_size(ifdk_plan p, int q_dtype, size_t *view_bytes, int *rows, int *row_elems)
+{
+    if (!p) return IFDK_ERR_INVALID;
+    if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
+    if (!p->pk[q_dtype].path) return IFDK_ERR_UNSUPPORTED;
+    if (view_bytes) *view_bytes = packed_view_bytes(p, q_dtype);
+    if (rows) *rows = p->pk_rows;
+    if (row_elems) *row_elems = p->pk_nu;
+    return IFDK_OK;
+}
+
+int ifdk_pack_views(ifdk_plan p, const void *Q, int q_dtype, int view_count, void *Qp, void *stream)
+{
+    if (!p || !Q || !Qp) return IFDK_ERR_INVALID;
+    if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
+    if (view_count < 0 || view_count > p->g.np) return IFDK_ERR_INVALID;
+    if (!p->pk[q_dtype].path) return IFDK_ERR_UNSUPPORTED;
+    if (((uintptr_t)Q & 15) || ((uintptr_t)Qp & 15)) return IFDK_ERR_ALIGNMENT;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return IFDK_ERR_CUDA;
+    return launch_pack(p, Q, q_dtype, view_count, Qp, (cudaStream_t)stream);
+}
+
+int ifdk_backproject_packed(ifdk_plan p, const void *Qp, int q_dtype, int view_begin, int view_count, float *vol,
+                            void *stream)
+{
+    int rc = check_backproject_args(p, Qp, q_dtype, view_begin, view_count, vol);
+    if (rc != IFDK_OK) return rc;
+    if (!p->pk[q_dtype].path) return IFDK_ERR_UNSUPPORTED;
+    if (view_count == 0) return IFDK_OK;
+    return launch_backproject_packed(p, Qp, q_dtype, view_begin, view_count, 0, p->g.np, vol, (cudaStream_t)stream);
+}
+
+int ifdk_set_view_pairing(ifdk_plan p, int enable)
+{
+    if (!p || (enable != 0 && enable != 1)) return IFDK_ERR_INVALID;
+    p->use_half_turn = enable != 0;
+    return IFDK_OK;
+}
+
 int ifdk_project(ifdk_plan p, const float *vol, float *P, int view_begin, int view_count, void *stream)
 {
     if (!p || !vol || !P) return IFDK_ERR_INVALID;
@@ -329,6 +376,48 @@ int ifdk_backproject_info(ifdk_plan p, int q_dtype, int64_t info[8])
     if (!p || !info) return IFDK_ERR_INVALID;
     if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
     fill_info(p, p->bp[q_dtype], info);
+    return IFDK_OK;
+}
+
+// Launch of a full-range packed back-projection: half-turn pairs when they apply.
+static void fill_packed_info(const ifdk_plan_s *p, int q_dtype, int64_t *info)
+{
+    const bool pairs = p->use_half_turn && p->pk2[q_dtype].path;
+    const PkLaunch &b = pairs ? p->pk2[q_dtype] : p->pk[q_dtype];
+    info[0] = b.path ? (pairs ? 2 : 1) : 0;
+    info[1] = b.bw;
+    info[2] = b.box_h;
+    info[3] = b.pairs;
+    info[4] = b.stages;
+    info[5] = (int64_t)b.smem;
+    info[6] = (int64_t)b.grid_x * b.grid_y;
+    info[7] = b.fold_w;
+    info[8] = b.align;
+    info[9] = p->pk_rows;
+    info[10] = p->pk_nu;
+    info[11] = p->pk_row0;
+}
+
+int ifdk_backproject_packed_info(ifdk_plan p, int q_dtype, int64_t info[12])
+{
+    if (!p || !info) return IFDK_ERR_INVALID;
+    if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
+    fill_packed_info(p, q_dtype, info);
+    return IFDK_OK;
+}
+
+int ifdk_query_packed(const ifdk_geometry *g, int q_dtype, int view_pairing, int64_t info[12])
+{
+    if (!info || (view_pairing != 0 && view_pairing != 1)) return IFDK_ERR_INVALID;
+    if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
+    int rc = validate(g);
+    if (rc != IFDK_OK) return rc;
+    ifdk_plan_s tmp;
+    rc = init_host_plan(&tmp, g);
+    if (rc != IFDK_OK) return rc;
+    plan_packed(&tmp);
+    tmp.use_half_turn = view_pairing != 0;
+    fill_packed_info(&tmp, q_dtype, info);
     return IFDK_OK;
 }
 

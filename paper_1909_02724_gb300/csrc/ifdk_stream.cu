@@ -10,10 +10,17 @@
 //                 of each host view), record ev_copy[h];
 //   `stream`:     wait ev_copy[h], back-project the chunk from the half
 //                 (ifdk_backproject_views addressing), record ev_bp[h].
+// Packed path (staging large enough, packed views available): after the copy
+// lands, the chunk is packed on `stream` into the half's packed part and the
+// packed kernels run on it; with half-turn pairing the views that pair up go
+// first, in pair chunks (views [s0, s0 + n) and [s0 + np/2, s0 + np/2 + n)
+// copied side by side), then the unpaired views.
 // The first copy waits for an event recorded on `stream` at entry, so it
 // never overwrites staging that earlier work on `stream` still reads.  Every
 // copy is waited for by a later back-projection on `stream`, so work issued
 // on `stream` after this call sees every copy complete.
+#include <vector>
+
 #include "ifdk_device.cuh"
 #include "ifdk_internal.h"
 
@@ -42,23 +49,47 @@ extern "C" int ifdk_backproject_host(ifdk_plan p, const void *Q_host, int q_dtyp
     const unsigned char *src0 = static_cast<const unsigned char *>(Q_host) + (size_t)host_row0 * g.nu * es;
     if (cudaEventRecord(p->ev_start, s) != cudaSuccess || cudaStreamWaitEvent(cs, p->ev_start, 0) != cudaSuccess)
         return IFDK_ERR_CUDA;
-    const int nchunks = (view_count + chunk_views - 1) / chunk_views;
-    for (int c = 0; c < nchunks; ++c) {
-        const int h = c & 1;
-        const int v0 = view_begin + c * chunk_views;
-        const int nvc = std::min(chunk_views, view_begin + view_count - v0);
-        unsigned char *dst = static_cast<unsigned char *>(staging) + h * half_bytes;
-        if (c >= 2 && cudaStreamWaitEvent(cs, p->ev_bp[h], 0) != cudaSuccess) return IFDK_ERR_CUDA;
+    // packed path: the second part of the staging holds the packed halves
+    const size_t pk_view = p->pk[q_dtype].path ? packed_view_bytes(p, q_dtype) : 0;
+    const size_t pk_half = (size_t)chunk_views * pk_view;
+    const bool packed = pk_view > 0 && staging_bytes >= 2 * (half_bytes + pk_half);
+    struct Chunk { int s0, n, paired; };
+    std::vector<Chunk> chunks;
+    const int b = view_begin, e = view_begin + view_count, h = g.np / 2;
+    int m = b;
+    if (packed && p->use_half_turn && p->pk2[q_dtype].path && chunk_views >= 2) split_half_turn(g.np, b, e, &m);
+    for (int s0 = b; s0 < m; s0 += chunk_views / 2) chunks.push_back({s0, std::min(chunk_views / 2, m - s0), 1});
+    const int r0[2] = {m, m == b ? e : m + h}, r1[2] = {m == b ? e : b + h, e};
+    for (int r = 0; r < 2; ++r)
+        for (int s0 = r0[r]; s0 < r1[r]; s0 += chunk_views) chunks.push_back({s0, std::min(chunk_views, r1[r] - s0), 0});
+    auto copy = [&](unsigned char *dst, int v0, int nvc) {
         const unsigned char *src = src0 + (size_t)v0 * host_view_bytes;
-        const cudaError_t ce =
-            host_nv == g.nv ? cudaMemcpyAsync(dst, src, (size_t)nvc * view_bytes, cudaMemcpyHostToDevice, cs)
-                            : cudaMemcpy2DAsync(dst, view_bytes, src, host_view_bytes, view_bytes, (size_t)nvc,
-                                                cudaMemcpyHostToDevice, cs);
-        if (ce != cudaSuccess || cudaEventRecord(p->ev_copy[h], cs) != cudaSuccess || cudaStreamWaitEvent(s, p->ev_copy[h], 0) != cudaSuccess)
+        return host_nv == g.nv ? cudaMemcpyAsync(dst, src, (size_t)nvc * view_bytes, cudaMemcpyHostToDevice, cs)
+                               : cudaMemcpy2DAsync(dst, view_bytes, src, host_view_bytes, view_bytes, (size_t)nvc,
+                                                   cudaMemcpyHostToDevice, cs);
+    };
+    for (size_t c = 0; c < chunks.size(); ++c) {
+        const int hb = (int)(c & 1);
+        const Chunk k = chunks[c];
+        const int nq = k.paired ? 2 * k.n : k.n;   // views in the half
+        unsigned char *dst = static_cast<unsigned char *>(staging) + hb * half_bytes;
+        if (c >= 2 && cudaStreamWaitEvent(cs, p->ev_bp[hb], 0) != cudaSuccess) return IFDK_ERR_CUDA;
+        cudaError_t ce = copy(dst, k.s0, k.n);
+        if (ce == cudaSuccess && k.paired) ce = copy(dst + (size_t)k.n * view_bytes, k.s0 + h, k.n);
+        if (ce != cudaSuccess || cudaEventRecord(p->ev_copy[hb], cs) != cudaSuccess ||
+            cudaStreamWaitEvent(s, p->ev_copy[hb], 0) != cudaSuccess)
             return IFDK_ERR_CUDA;
-        rc = launch_backproject(p, dst, q_dtype, v0, nvc, v0, nvc, vol, s);
+        if (packed) {
+            unsigned char *pk = static_cast<unsigned char *>(staging) + 2 * half_bytes + hb * pk_half;
+            rc = launch_pack(p, dst, q_dtype, nq, pk, s);
+            if (rc == IFDK_OK)
+                rc = k.paired ? launch_packed_pairs(p, pk, q_dtype, k.s0, k.n, k.s0, k.n, nq, vol, s)
+                              : launch_backproject_packed(p, pk, q_dtype, k.s0, k.n, k.s0, nq, vol, s);
+        } else {
+            rc = launch_backproject(p, dst, q_dtype, k.s0, k.n, k.s0, k.n, vol, s);
+        }
         if (rc != IFDK_OK) return rc;
-        if (cudaEventRecord(p->ev_bp[h], s) != cudaSuccess) return IFDK_ERR_CUDA;
+        if (cudaEventRecord(p->ev_bp[hb], s) != cudaSuccess) return IFDK_ERR_CUDA;
     }
     return IFDK_OK;
 }

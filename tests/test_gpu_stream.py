@@ -75,13 +75,13 @@ def test_host_streaming_is_bit_identical(dtype):
     assert float((ref - whole).abs().max()) <= 1e-6 * float(whole.abs().max())
     Qh = Q.cpu().pin_memory()
     vol = torch.zeros((g.nx, g.ny, g.nz), device="cuda")
-    plan.backproject_host(Qh, vol, chunk_views=7)                # 6 chunks, the last one of 5 views
+    plan.backproject_host(Qh, vol, chunk_views=7, packed=False)  # 6 chunks, the last one of 5 views
     torch.cuda.synchronize()
     assert torch.equal(vol, ref)
     # view subsets accumulate; one chunk larger than the range
     vol2 = torch.zeros_like(vol)
-    plan.backproject_host(Qh, vol2, chunk_views=64, view_begin=0, view_count=11)
-    plan.backproject_host(Qh, vol2, chunk_views=4, view_begin=11, view_count=29)
+    plan.backproject_host(Qh, vol2, chunk_views=64, view_begin=0, view_count=11, packed=False)
+    plan.backproject_host(Qh, vol2, chunk_views=4, view_begin=11, view_count=29, packed=False)
     torch.cuda.synchronize()
     assert float((vol2 - whole).abs().max()) <= 1e-6 * float(whole.abs().max())
     assert plan.device_status() == 0
@@ -100,9 +100,15 @@ def test_row_window_streamed_out_of_full_height_views():
     assert float((ref_cut - ref_full).norm() / ref_full.norm()) <= 2e-6
     Qh = Q.cpu().pin_memory()                                     # full-height host views
     vol = torch.zeros_like(ref_cut)
-    cut_plan.backproject_host(Qh, vol, chunk_views=8, host_row0=r0)
+    cut_plan.backproject_host(Qh, vol, chunk_views=8, host_row0=r0, packed=False)
     torch.cuda.synchronize()
     assert torch.equal(vol, ref_cut)
+    # the packed streaming path on the same rows: the same sum up to rounding order
+    vol_p = torch.zeros_like(ref_cut)
+    cut_plan.backproject_host(Qh, vol_p, chunk_views=8, host_row0=r0)
+    torch.cuda.synchronize()
+    # (the packed FP16 kernel also takes the v-lerp in half2)
+    assert float((vol_p - ref_cut).norm() / ref_cut.norm()) <= 5e-4
 
 
 def test_host_streaming_rejects_bad_arguments():

@@ -160,3 +160,141 @@ def _gpu_test_geoms():
 def test_fold_windows_of_every_gpu_test_geometry(dtype):
     for name, g in _gpu_test_geoms().items():
         check_fold_windows(g, dtype)
+
+
+# ---------------------------------------------------------------------------
+# Packed views: the packed kernel's windows (emulated like the fold kernel's)
+# hold every tap, and every tap row a written voxel reads is a packed row
+# unless both it and its mirror lie outside the detector (then 0 is right).
+
+def check_packed_windows(g, q_dtype, view_pairing=True, blocks=None):
+    info = B.ifdk_query_packed(g, q_dtype, view_pairing)
+    if info["path"] == 0:
+        return info
+    H, BW, L, AL = info["box_h"], info["box_w"], info["z_per_thread"], info["align"]
+    r0, R = info["row0"], info["rows"]
+    t = _terms(g)
+    cx, cy, cz = (g.nx - 1) / 2, (g.ny - 1) / 2, (g.nz - 1) / 2
+    uc, vc = (g.nu - 1) / 2 + g.off_u / g.du, (g.nv - 1) / 2 + g.off_v / g.dv
+    two_vc = int(round(2 * vc))
+    ny_cols = g.ny // 2 if info["path"] == 2 else g.ny
+    tiles_x, tiles_y = -(-g.nx // TILE), -(-ny_cols // TILE)
+    npairs = (g.nz + 1) // 2
+    zblocks = -(-npairs // L)
+    assert info["blocks"] == tiles_x * tiles_y * zblocks
+    if blocks is None:
+        blocks = [(bx, by, bz) for bx in range(tiles_x) for by in range(tiles_y) for bz in range(zblocks)]
+    tx, ty = np.meshgrid(np.arange(TILE), np.arange(TILE), indexing="ij")
+    tx, ty = tx.ravel(), ty.ravel()
+    p = np.arange(L)
+    for bx, by, bz in blocks:
+        i0, j0, k0 = bx * TILE, by * TILE, bz * L
+        kp0 = k0 - cz
+        ia, ib, ja, jb = i0 - cx, i0 + TILE - 1 - cx, j0 - cy, j0 + TILE - 1 - cy
+        ci, cj = np.array([ia, ib, ia, ib]), np.array([ja, ja, jb, jb])
+        zc = t["C0"][:, None] * ci + t["C1"][:, None] * cj + t["C3"][:, None]
+        ucn = (t["A0"][:, None] * ci + t["A1"][:, None] * cj) / zc
+        u_lo, z_lo, z_hi = ucn.min(1), zc.min(1), zc.max(1)
+        e0, e1 = t["B2"] * kp0, t["B2"] * (kp0 + L - 1)
+        v_lo = np.minimum(np.minimum(e0 / z_lo, e0 / z_hi), np.minimum(e1 / z_lo, e1 / z_hi))
+        u0a = np.floor((np.floor(uc + u_lo) - MARGIN + 1) / AL) * AL - 1
+        # the TMA box starts at element u0a + 1: 4 values of q_dtype each, 16-byte aligned
+        assert np.all((4 * (u0a + 1) * (4 if q_dtype == B.IFDK_F32 else 2)) % 16 == 0)
+        v0 = np.floor(vc + v_lo) - MARGIN
+        ip = (i0 + tx) - cx
+        jp = (j0 + ty) - cy
+        z = t["C0"][:, None] * ip + t["C1"][:, None] * jp + t["C3"][:, None]
+        f = 1.0 / z
+        ul = (t["A0"][:, None] * ip + t["A1"][:, None] * jp) * f + (uc - u0a)[:, None]
+        # element cu = floor(ul) holds columns cu and cu + 1
+        assert ul.min() >= 0.01 and ul.max() < BW - 0.01, (bx, by, bz, ul.min(), ul.max(), BW)
+        sig = t["B2"][:, None] * f
+        vl = (vc - v0)[:, None, None] + sig[:, :, None] * (kp0 + p)[None, None, :]
+        assert vl.min() >= 0.01 and vl.max() < H - 1 - 0.01, (bx, by, bz, vl.min(), vl.max(), H)
+        # packed element u0a + floor(ul) (column c = element - 1 + 1 ... held from column -1 on)
+        cols = u0a[:, None] + np.floor(ul)
+        c_in = (cols >= -1) & (cols < -1 + info["row_elems"])
+        c_off = (cols + 1 < 0) | (cols >= g.nu)          # both taps c, c + 1 off the detector
+        assert np.all(c_in | c_off), (bx, by, bz)
+        written = (k0 + p) < npairs
+        rows = v0[:, None, None] + np.floor(vl[:, :, written])
+        for rr in (rows, rows + 1):
+            inside = (rr >= r0) & (rr < r0 + R)
+            off_det = ((rr < 0) | (rr >= g.nv)) & ((two_vc - rr < 0) | (two_vc - rr >= g.nv))
+            assert np.all(inside | off_det), (bx, by, bz)
+    return info
+
+
+@pytest.mark.parametrize("dtype", [B.IFDK_F32, B.IFDK_F16, B.IFDK_BF16])
+@pytest.mark.parametrize("geom", [
+    scaled_geometry(64, 64, 64),
+    scaled_geometry(40, 56, 24, nz=50, n_det_v=48),
+    scaled_geometry(33, 48, 16, nz=33),
+    circular(10, 64, 48, 1.5, 1.5, 36, 28, 22, 1.0, off_u=-0.4, off_v=0.75),
+    circular(10, 64, 48, 1.5, 1.5, 36, 28, 22, 1.0, off_u=0.2, off_v=-0.75),
+    circular(12, 64, 48, 1.5, 1.5, 36, 28, 22, 1.0, off_v=-4.5),
+    circular(9, 96, 80, 0.5, 0.5, 24, 24, 20, 0.5),
+])
+def test_packed_windows_contain_every_tap(geom, dtype):
+    for pairing in (True, False):
+        info = check_packed_windows(geom, dtype, view_pairing=pairing)
+        assert info["path"] == (2 if pairing and geom.ny % 2 == 0 and geom.np % 2 == 0 else 1)
+
+
+def test_packed_path_declines_wide_footprints():
+    """A strongly magnified scan (window wider than the largest box) has no
+    packed path; ifdk_backproject's general kernel serves it."""
+    g = circular(6, 16, 16, 1.4, 1.3, 8, 8, 8, 1.1, 1.0, 0.9, sid=60.0, sdd=95.0, start=0.3)
+    assert B.ifdk_query_packed(g, B.IFDK_F32)["path"] == 0
+    assert B.ifdk_query_backproject(g, B.IFDK_F32)["path"] == 0
+
+
+@pytest.mark.parametrize("name", ["fdk512", "grad256", "fdk2048", "slab4096"])
+def test_packed_windows_large_workloads(name):
+    g = workload(name).geom
+    rng = np.random.default_rng(1)
+    if g.np > 512:   # subsample views for the largest scans
+        g = g.with_(angles=g.angles[::4])
+    for dt in (B.IFDK_F32, B.IFDK_F16):
+        for pairing in (True, False):
+            info = B.ifdk_query_packed(g, dt, pairing)
+            ny_cols = g.ny // 2 if info["path"] == 2 else g.ny
+            tx, ty = -(-g.nx // TILE), -(-ny_cols // TILE)
+            zb = -(-((g.nz + 1) // 2) // info["z_per_thread"])
+            blocks = {(0, 0, 0), (tx - 1, ty - 1, zb - 1), (tx // 2, ty // 2, zb // 2), (0, ty - 1, 0),
+                      (tx - 1, 0, zb - 1)}
+            blocks |= {(int(rng.integers(tx)), int(rng.integers(ty)), int(rng.integers(zb))) for _ in range(6)}
+            info = check_packed_windows(g, dt, pairing, sorted(blocks))
+            assert info["path"] == (2 if pairing else 1), (name, dt, info)
+
+
+def test_half_turn_pairing_detection():
+    """Path 2 (half-turn view pairs) exactly when every view s < np/2 has a
+    partner s + np/2 turned by pi and ny is even; otherwise single views."""
+    g = scaled_geometry(32, 48, 16)
+    assert B.ifdk_query_packed(g, B.IFDK_F32)["path"] == 2
+    assert B.ifdk_query_packed(g, B.IFDK_F32, view_pairing=False)["path"] == 1
+    assert B.ifdk_query_packed(g.with_(ny=31), B.IFDK_F32)["path"] == 1                  # odd ny
+    odd = circular(15, 48, 48, 96 / 48, 96 / 48, 32, 32, 32, 2.0)
+    assert B.ifdk_query_packed(odd, B.IFDK_F32)["path"] == 1                              # odd np
+    short = g.with_(angles=np.linspace(0, np.pi + 0.4, g.np, endpoint=False))
+    assert B.ifdk_query_packed(short, B.IFDK_F32)["path"] == 1                            # no partner at +pi
+    jitter = g.angles.copy()
+    jitter[g.np // 2 + 3] += 1e-6
+    assert B.ifdk_query_packed(g.with_(angles=jitter), B.IFDK_F32)["path"] == 1
+    assert B.ifdk_query_packed(g.with_(angles=g.angles + 0.37), B.IFDK_F32)["path"] == 2   # any start angle
+    # packed views need the mirror path: centred volume, 2 vc integral
+    assert B.ifdk_query_packed(g.with_(vol_off_z=1.0), B.IFDK_F32)["path"] == 0
+    assert B.ifdk_query_packed(g.with_(off_v=0.3 * g.dv), B.IFDK_F32)["path"] == 0
+
+
+def test_packed_rows_cover_mirrors_above_the_detector():
+    """r0 = min(0, 2 vc - (nv - 1)): with the principal point above the centre,
+    rows above the detector whose mirrors are on it are packed too."""
+    for off_px, r0 in [(0.0, 0), (0.5, 0), (-0.5, -1), (-3.0, -6)]:
+        g = circular(12, 64, 48, 1.5, 1.5, 36, 28, 22, 1.0, off_v=off_px * 1.5)
+        info = B.ifdk_query_packed(g, B.IFDK_F32)
+        vc = (g.nv - 1) / 2 + off_px
+        assert info["row0"] == r0
+        assert info["rows"] == int(np.floor(vc)) + 3 - r0
+        assert info["row_elems"] == g.nu + 2          # columns -1 .. nu - 1, rounded up to even
