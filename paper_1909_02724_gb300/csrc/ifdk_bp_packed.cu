@@ -33,9 +33,11 @@
 //     s to view s + P), so the two views' elements of a row sit side by side;
 //     TMA's zero fill implements "taps outside the detector read 0";
 //   * a ring of stages (one group each) paced by mbarriers: full = the box
-//     landed, empty = every warp finished the group; warp 0 refills the
-//     stage released two groups earlier, so up to stages - 1 groups are in
-//     flight and warps never meet at a block-wide barrier;
+//     landed, empty = every warp finished the group.  At group t, warp
+//     t mod 8 refills the stage group t - 2 used with group t - 2 + stages
+//     (the refill's latency, a wait and a few dependent loads, rotates over
+//     the warps), so up to stages - 1 groups are in flight and warps never
+//     meet at a block-wide barrier;
 //   * consecutive pairs step about one detector row (the magnification), so
 //     when every lane of a warp steps less than a row, a pair loads only its
 //     upper row and takes the lower one from the previous pair;
@@ -291,10 +293,11 @@ __device__ __forceinline__ void write_run(const PkArgs &a, int k0, int i, int j,
 }
 
 // Shared-memory map (offsets from a 128-byte aligned base): full barriers at
-// 8 s, empty barriers at 64 + 8 s, the abort flag at 128, stages from 256;
-// a stage is its PkGeom (128 bytes reserved) followed by the box.
-constexpr uint32_t kPkFull = 0, kPkEmpty = 64, kPkAbort = 128, kPkStage0 = 256, kPkBox = 128;
-static_assert(kPkMaxStages * 8 <= 64, "barrier map");
+// 8 s, empty barriers at 64 + 8 s, the abort flag at 128, the last group
+// issued into each stage at 160 + 4 s, stages from 256; a stage is its
+// PkGeom (128 bytes reserved) followed by the box.
+constexpr uint32_t kPkFull = 0, kPkEmpty = 64, kPkAbort = 128, kPkLast = 160, kPkStage0 = 256, kPkBox = 128;
+static_assert(kPkMaxStages * 8 <= 64 && kPkLast + 4 * kPkMaxStages <= kPkStage0, "shared-memory map");
 
 template <typename T, int NV, int BW, int L>
 __global__ void __launch_bounds__(kThreads, NV == 1 ? 3 : 2)
@@ -367,6 +370,7 @@ __global__ void __launch_bounds__(kThreads, NV == 1 ? 3 : 2)
         sts_f32x4(sg + 16, t1);
         sts_f32x4(sg + 32, make_float4(w0, a.uc - (float)u0a, a.vc - (float)v0, w1));
         const uint32_t bar = s0 + kPkFull + 8u * st;
+        sts_u32(s0 + kPkLast + 4u * st, (uint32_t)t);
         fence_proxy_async_shared();
         mbar_arrive_expect_tx(bar, a.box_tx_bytes);
         const int q = s - a.q_view0;
@@ -376,9 +380,10 @@ __global__ void __launch_bounds__(kThreads, NV == 1 ? 3 : 2)
             tma_load_3d(sg + kPkBox, &tmap, 4 * (u0a + 1), v0 - a.row0, q, bar);
     };
 
-    int issued = min(S, ngroups);   // groups issued so far (tracked by warp 0)
+    // the prologue fills every stage (its lane also records them as the last
+    // group issued into each stage, which an aborting warp drains)
     if (warp == 0 && lane == 0)
-        for (int t = 0; t < issued; ++t) issue(t);
+        for (int t = 0; t < min(S, ngroups); ++t) issue(t);
 
     float2 acc[NV][L];
 #pragma unroll
@@ -395,14 +400,14 @@ __global__ void __launch_bounds__(kThreads, NV == 1 ? 3 : 2)
         const int st = t % S;
         const uint32_t parity = (uint32_t)(t / S) & 1u;
         // refill the stage group t - 2 used (every warp finished it by now, or soon)
-        if (warp == 0 && t >= 2 && issued < ngroups) {
+        const int gn = t - 2 + S;
+        if (t >= 2 && gn < ngroups && (t & (kThreads / 32 - 1)) == warp) {
             bool e = true;
             if (lane == 0) {
                 e = mbar_wait_lim(s0 + kPkEmpty + 8u * ((t - 2) % S), (uint32_t)((t - 2) / S) & 1u, a.wait_ns);
-                if (e) issue(issued);
+                if (e) issue(gn);
             }
             ok = __shfl_sync(0xffffffffu, e, 0) != 0;
-            ++issued;
             if (!ok) return;
         }
         ok = __all_sync(0xffffffffu, mbar_wait_lim(s0 + kPkFull + 8u * st, parity, a.wait_ns));
@@ -444,12 +449,16 @@ __global__ void __launch_bounds__(kThreads, NV == 1 ? 3 : 2)
         for (int t = 0; ok && t < ngroups; ++t) group(t, std::false_type{});
     }
     if (!ok) {
-        // record the timeout; warp 0 keeps shared memory alive until every box it
-        // issued has landed (a stage holds at most one box in flight)
-        if (lane == 0) atomicOr(a.status, kStatusTimeout);
-        if (warp == 0 && lane == 0)
-            for (int t = max(0, issued - S); t < issued; ++t)
-                mbar_wait_lim(s0 + kPkFull + 8u * (t % S), (uint32_t)(t / S) & 1u, a.wait_ns);
+        // record the timeout; every exiting warp waits (bounded) for the last box
+        // issued into each stage, so the last warp to leave the block leaves no
+        // copy in flight (a warp issues nothing after it left)
+        if (lane == 0) {
+            atomicOr(a.status, kStatusTimeout);
+            for (int st = 0; st < min(S, ngroups); ++st) {
+                const int t = (int)lds_u32_v(s0 + kPkLast + 4u * st);
+                mbar_wait_lim(s0 + kPkFull + 8u * st, (uint32_t)(t / S) & 1u, a.wait_ns);
+            }
+        }
         return;
     }
     if (ci < a.nx && cj < a.ny_cols) {
