@@ -39,8 +39,8 @@
 //     the warps), so up to stages - 1 groups are in flight and warps never
 //     meet at a block-wide barrier;
 //   * consecutive pairs step about one detector row (the magnification), so
-//     when every lane of a warp steps less than a row, a pair loads only its
-//     upper row and takes the lower one from the previous pair;
+//     a pair loads only its upper row and takes the lower one from the
+//     previous pair (after a step of two rows, it loads both);
 //   * FP32 accumulation in registers over all views, one read-modify-write of
 //     each thread's z-runs at the end (vectorised, 64-bit offsets, k-major).
 //   FP32 / BF16 storage: taps are interpolated in packed f32x2 arithmetic
@@ -212,11 +212,15 @@ template <> struct Tap<__nv_bfloat16> {
 // The z-run of one (column, view group): pair p samples box rows n_p, n_p + 1
 // at v_p = vb + p sig (window coordinates).  The box holds NV views side by
 // side in each row (HB bytes apart, rows ROWB bytes apart); view 0's taps go
-// to a0 with weight W0, view 1's to a1 with weight W1.  With REUSE (every
-// lane of the warp has sig < 1, so n_{p+1} - n_p is 0 or 1) a pair loads only
-// row n_p + 1 and takes row n_p from the previous pair's upper row when it
-// moved up; otherwise it loads both rows.
-template <typename T, int NV, int L, uint32_t ROWB, uint32_t HB, bool REUSE>
+// to a0 with weight W0, view 1's to a1 with weight W1.  Row reuse by the
+// warp's largest step (every lane votes): STEP1 (all sig < 1: n_{p+1} - n_p
+// is 0 or 1) loads only row n_p + 1 and takes row n_p from the previous
+// pair; STEP2 (sig < 2, which the plan guarantees: steps 0, 1 or 2) does the
+// same and loads row n_p as well only after a step of 2 (a predicated load:
+// less shared-memory traffic, for FP32 taps); ANY loads both rows.
+enum class Reuse { STEP1, STEP2, ANY };
+
+template <typename T, int NV, int L, uint32_t ROWB, uint32_t HB, Reuse MODE>
 __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], const unsigned char *sm,
                                           uint32_t base, float sig, float vb, float2 du2, __half2 duh, float2 W0,
                                           float2 W1)
@@ -239,7 +243,13 @@ __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], cons
         e = sm + (base + tn * ROWB);
         const float2 dv2 = make_float2(dv, dv);
         const __half2 dvh = __float2half2_rn(dv);
-        if constexpr (REUSE) {
+        if constexpr (MODE == Reuse::ANY) {
+#pragma unroll
+            for (int n = 0; n < NV; ++n) {
+                lo[n] = Tap<T>::row(e + n * HB, du2, duh);
+                hi[n] = Tap<T>::row(e + ROWB + n * HB, du2, duh);
+            }
+        } else if constexpr (MODE == Reuse::STEP1) {
             const bool moved = tn != tv;
             tv = tn;
 #pragma unroll
@@ -249,10 +259,15 @@ __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], cons
                 hi[n] = hn;
             }
         } else {
+            const uint32_t step = tn - tv;
+            tv = tn;
 #pragma unroll
             for (int n = 0; n < NV; ++n) {
-                lo[n] = Tap<T>::row(e + n * HB, du2, duh);
-                hi[n] = Tap<T>::row(e + ROWB + n * HB, du2, duh);
+                const R hn = Tap<T>::row(e + ROWB + n * HB, du2, duh);
+                R ln = step != 0 ? hi[n] : lo[n];
+                if (step == 2) ln = Tap<T>::row(e + n * HB, du2, duh);
+                lo[n] = ln;
+                hi[n] = hn;
             }
         }
         a0[p] = Tap<T>::accum(a0[p], lo[0], hi[0], dv2, dvh, W0);
@@ -432,11 +447,13 @@ __global__ void __launch_bounds__(kThreads, NV == 1 ? 3 : 2)
         const __half2 duh = __float2half2_rn(du);
         float2(&c0)[L] = SWAP ? acc[NV - 1] : acc[0];
         float2(&c1)[L] = SWAP ? acc[0] : acc[NV - 1];
-        // sig < 1 - 2^-10 keeps fp32 rounding of v_{p+1} - v_p below one row
+        // sig < 1 - 2^-10 keeps fp32 rounding of v_{p+1} - v_p below one row; the
+        // plan keeps every sig below 1.9 (two rows at most)
+        constexpr Reuse WIDE = sizeof(T) == 4 ? Reuse::STEP2 : Reuse::ANY;
         if (__all_sync(0xffffffffu, sig < 0.9990234375f))
-            pair_loop<T, NV, L, ROWB, HB, true>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1);
+            pair_loop<T, NV, L, ROWB, HB, Reuse::STEP1>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1);
         else
-            pair_loop<T, NV, L, ROWB, HB, false>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1);
+            pair_loop<T, NV, L, ROWB, HB, WIDE>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1);
         __syncwarp();
         if (lane == 0) mbar_arrive(s0 + kPkEmpty + 8u * st);
     };
@@ -530,6 +547,7 @@ PkLaunch size_packed(const ifdk_plan_s *p, int q_dtype, int nv)
     const double wu = g.sdd / g.du * et * (1.0 / cmin + 2.0 * rxy / (cmin * cmin));
     const double kmax = std::max(cz, (double)zblocks * L - 1 - cz);
     const double b2 = g.sdd * g.dz / g.dv;
+    if (b2 / cmin >= 1.9) return b;   // rows per voxel step (the largest sig) below 2
     const double hv = b2 * (L - 1) / cmin + b2 * kmax * et / (cmin * cmin);
     b.fold_w = (int)std::ceil(wu) + 2 * kPkMargin + 2;
     b.box_h = (int)std::ceil(hv) + 2 * kPkMargin + 3;

@@ -298,3 +298,11 @@ def test_packed_rows_cover_mirrors_above_the_detector():
         assert info["row0"] == r0
         assert info["rows"] == int(np.floor(vc)) + 3 - r0
         assert info["row_elems"] == g.nu + 2          # columns -1 .. nu - 1, rounded up to even
+
+
+def test_packed_path_needs_row_steps_below_two():
+    """The packed kernel reuses rows for steps of at most two rows per voxel:
+    the plan declines scans whose largest step D dz / (dv z_min) reaches 1.9."""
+    g = circular(8, 64, 64, 0.5, 0.5, 16, 16, 16, 0.5, dz=0.5)
+    assert B.ifdk_query_packed(g, B.IFDK_F32)["path"] in (1, 2)      # step ~1.5
+    assert B.ifdk_query_packed(g.with_(dz=0.7), B.IFDK_F32)["path"] == 0   # step ~2.1
