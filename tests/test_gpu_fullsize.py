@@ -48,39 +48,52 @@ def slices(g, ks, step):
 
 
 def run(name, dtypes, vox):
+    """Every storage type through both back-projectors: the packed path (pack +
+    packed kernel with half-turn view pairs: what bench.py times) and the
+    standard-layout kernel."""
     from paper_1909_02724_gb300.binding import Plan
     w = workload(name)
     g = w.geom
     E = workload_projections_gpu(w)
     plan = Plan(g)
     ref = oracle_on_sample(g, E, vox)
-    vols = {}
+    idx = [torch.from_numpy(vox[:, c]).cuda() for c in range(3)]
+    f32_vol = None
     for key in dtypes:
         tdt = getattr(torch, DTYPES[key])
         Q = plan.filter(E, dtype=tdt)
-        vol = torch.zeros((g.nx, g.ny, g.nz), device="cuda")
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        plan.backproject(Q, vol)
-        torch.cuda.synchronize()
-        print(f"{name} {key}: back-projection {g.updates / (time.perf_counter() - t) / 2**30:.0f} GUPS")
-        del Q
-        assert plan.device_status() == 0
-        v = vol[torch.from_numpy(vox[:, 0]).cuda(), torch.from_numpy(vox[:, 1]).cuda(),
-                torch.from_numpy(vox[:, 2]).cuda()].double().cpu().numpy()
-        err = float(np.linalg.norm(v - ref) / np.linalg.norm(ref))
-        vmax = float(vol.abs().max())
-        if key == "f32":
-            assert err <= 1e-5, (name, key, err)
-            assert float(np.max(np.abs(v - ref))) <= 1e-4 * vmax
-        else:
-            assert err <= 2e-3, (name, key, err)
-        vols[key] = vol
-        if key != "f32" and "f32" in vols:
-            full = float((vol - vols["f32"]).norm() / vols["f32"].norm())
-            assert full <= 2e-3, (name, key, full)
-            del vols[key]
-    return vols
+        for path in ("standard", "packed"):
+            vol = torch.zeros((g.nx, g.ny, g.nz), device="cuda")
+            if path == "packed":
+                Qp = plan.pack(Q)
+                del Q
+                Q = None
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            if path == "packed":
+                plan.backproject_packed(Qp, vol)
+            else:
+                plan.backproject(Q, vol)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            assert plan.device_status() == 0
+            v = vol[idx[0], idx[1], idx[2]].double().cpu().numpy()
+            err = float(np.linalg.norm(v - ref) / np.linalg.norm(ref))
+            mx = float(np.max(np.abs(v - ref))) / float(vol.abs().max())
+            print(f"{name} {key} {path}: {g.updates / dt / 2**30:.0f} GUPS, rel-L2 {err:.2e}, max-abs/max {mx:.2e}")
+            if key == "f32":
+                assert err <= 1e-5, (name, key, path, err)
+                assert mx <= 1e-4, (name, key, path, mx)
+            else:
+                assert err <= 2e-3, (name, key, path, err)
+            if key == "f32" and path == "standard":
+                f32_vol = vol
+            elif f32_vol is not None:
+                full = float((vol - f32_vol).norm() / f32_vol.norm())
+                print(f"{name} {key} {path}: rel-L2 vs the FP32 standard volume {full:.2e}")
+                assert full <= 2e-3, (name, key, path, full)
+                del vol
+        del Qp
 
 
 def test_fdk512_all_storage_types():
