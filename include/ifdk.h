@@ -181,10 +181,11 @@ int ifdk_backproject_views(ifdk_plan p, const void *Qv, int q_dtype, int view_be
    i in [0, rows) and e in [0, row_elems), is detector row r = r0 + i with
    r0 = min(0, 2 v_c - (nv - 1)) (rows = floor(v_c) + 3 - r0) and column
    c = e - 1 (row_elems = nu + 1 rounded up to even) and holds
-     Q[r][c], Q[2 v_c - r][c], Q[r][c + 1], Q[2 v_c - r][c + 1],
-   each 0 where its row or column is outside the detector.  That is about
-   twice the bytes of a view of Q, and one shared-memory load then gives a
-   voxel pair both taps of a detector row.
+     Q[r][c], Q[2 v_c - r][c], Q[r][c+1] - Q[r][c], Q[2 v_c - r][c+1] - Q[2 v_c - r][c],
+   where Q reads 0 outside the detector; the differences are formed in FP32
+   from the stored values and rounded once to q_dtype.  That is about twice
+   the bytes of a view of Q; one shared-memory load then gives a voxel pair
+   both taps of a detector row, and interpolating along U is one FMA.
    ifdk_packed_size reports view_bytes (bytes of one packed view), rows and
    row_elems (any pointer may be NULL). */
 int ifdk_packed_size(ifdk_plan p, int q_dtype, size_t *view_bytes, int *rows, int *row_elems);

@@ -5,10 +5,12 @@
 // images about v_c (Theorem 1: v_mirror = 2 v_c - v).  A packed view stores
 // for row r in [r0, floor(v_c) + 3), r0 = min(0, 2 v_c - (nv - 1)) (rows
 // whose mirror lies on the detector), and column c in [-1, nu) the element
-//   (Q[r][c], Q[2vc-r][c], Q[r][c+1], Q[2vc-r][c+1])
-// (zero where a row or column lies outside the detector; column -1 carries
-// the first column as its right tap), so one shared-memory
-// load gives both voxels of a pair the two taps of a detector row.  Packing
+//   (Q[r][c], Q[2vc-r][c], Q[r][c+1] - Q[r][c], Q[2vc-r][c+1] - Q[2vc-r][c])
+// (Q read as zero where a row or column lies outside the detector; column -1
+// carries the first column as its right tap), so one shared-memory
+// load gives both voxels of a pair the two taps of a detector row, and the
+// interpolation along u is one FMA per pair (the difference is formed in
+// FP32 when packing, then stored in the storage type).  Packing
 // is one pass over Q (ifdk_pack_views); the back-projection then stages
 // windows of packed views with TMA and uses them as they land.
 //
@@ -172,8 +174,8 @@ template <> struct Tap<float> {
     using R = float2;
     __device__ __forceinline__ static R row(const unsigned char *e, float2 du2, __half2)
     {
-        const float4 q = *reinterpret_cast<const float4 *>(e);
-        return lerp2(make_float2(q.x, q.y), make_float2(q.z, q.w), du2);
+        const float4 q = *reinterpret_cast<const float4 *>(e);   // (taps at c, differences to c + 1)
+        return __ffma2_rn(du2, make_float2(q.z, q.w), make_float2(q.x, q.y));
     }
     __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2 dv2, __half2, float2 W2)
     {
@@ -186,8 +188,8 @@ template <> struct Tap<__half> {
     __device__ __forceinline__ static R row(const unsigned char *e, float2, __half2 duh)
     {
         const uint2 q = *reinterpret_cast<const uint2 *>(e);
-        const __half2 hx = *reinterpret_cast<const __half2 *>(&q.x), hy = *reinterpret_cast<const __half2 *>(&q.y);
-        return __hfma2(duh, __hsub2(hy, hx), hx);
+        const __half2 hx = *reinterpret_cast<const __half2 *>(&q.x), hd = *reinterpret_cast<const __half2 *>(&q.y);
+        return __hfma2(duh, hd, hx);
     }
     __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2, __half2 dvh, float2 W2)
     {
@@ -200,8 +202,8 @@ template <> struct Tap<__nv_bfloat16> {
     __device__ __forceinline__ static R row(const unsigned char *e, float2 du2, __half2)
     {
         const uint2 q = *reinterpret_cast<const uint2 *>(e);
-        return lerp2(make_float2(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xffff0000u)),
-                     make_float2(__uint_as_float(q.y << 16), __uint_as_float(q.y & 0xffff0000u)), du2);
+        return __ffma2_rn(du2, make_float2(__uint_as_float(q.y << 16), __uint_as_float(q.y & 0xffff0000u)),
+                          make_float2(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xffff0000u)));
     }
     __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2 dv2, __half2, float2 W2)
     {
@@ -485,7 +487,8 @@ __global__ void __launch_bounds__(kThreads, NV == 1 ? 3 : 2)
 }
 
 // Packing: element e of row r of view s, column c = e - 1:
-// (Q[r][c], Q[2vc-r][c], Q[r][c+1], Q[2vc-r][c+1]).
+// (Q[r][c], Q[2vc-r][c], Q[r][c+1] - Q[r][c], Q[2vc-r][c+1] - Q[2vc-r][c]),
+// the differences formed in FP32 and rounded once to T.
 __device__ __forceinline__ uint32_t bits16(__half x) { return __half_as_ushort(x); }
 __device__ __forceinline__ uint32_t bits16(__nv_bfloat16 x) { return __bfloat16_as_ushort(x); }
 __device__ __forceinline__ uint32_t bits16(float) { return 0u; }
@@ -497,7 +500,6 @@ struct PackArgs {
 template <typename T>
 __global__ void __launch_bounds__(256) pack_kernel(const T *__restrict__ Q, T *__restrict__ P, const PackArgs a)
 {
-    const T zero = T(0.0f);
     for (long long e = blockIdx.x * 256ll + threadIdx.x; e < a.n_elems; e += (long long)gridDim.x * 256) {
         const int c = (int)(e % a.nu_p) - 1;
         const long long sr = e / a.nu_p;
@@ -507,10 +509,12 @@ __global__ void __launch_bounds__(256) pack_kernel(const T *__restrict__ Q, T *_
         const int rm = a.two_vc - r;
         const bool dr = r >= 0 && r < a.nv, mr = rm >= 0 && rm < a.nv;
         const bool c0 = c >= 0 && c < a.nu, c1 = c + 1 < a.nu;   // c + 1 >= 0 always
-        const T v0 = dr && c0 ? qv[(long long)r * a.nu + c] : zero;
-        const T v1 = mr && c0 ? qv[(long long)rm * a.nu + c] : zero;
-        const T v2 = dr && c1 ? qv[(long long)r * a.nu + c + 1] : zero;
-        const T v3 = mr && c1 ? qv[(long long)rm * a.nu + c + 1] : zero;
+        const float q0 = dr && c0 ? Storage<T>::to_float(qv[(long long)r * a.nu + c]) : 0.0f;
+        const float q1 = mr && c0 ? Storage<T>::to_float(qv[(long long)rm * a.nu + c]) : 0.0f;
+        const float q2 = dr && c1 ? Storage<T>::to_float(qv[(long long)r * a.nu + c + 1]) : 0.0f;
+        const float q3 = mr && c1 ? Storage<T>::to_float(qv[(long long)rm * a.nu + c + 1]) : 0.0f;
+        const T v0 = Storage<T>::from_float(q0), v1 = Storage<T>::from_float(q1);
+        const T v2 = Storage<T>::from_float(q2 - q0), v3 = Storage<T>::from_float(q3 - q1);
         T *d = P + e * 4;
         if constexpr (sizeof(T) == 4) {
             *reinterpret_cast<float4 *>(d) = make_float4(v0, v1, v2, v3);
