@@ -78,6 +78,7 @@ struct PkArgs {
     int pair_view_off;                  // P
     int box_h, stages, row0;            // row0: detector row of packed row 0
     float cx, cy, cz, uc, vc;
+    float wscale, wunscale;             // power of two on the FDK weights (FP16: keeps W in range) and its inverse
     uint32_t stage_bytes, box_tx_bytes;
 };
 
@@ -172,12 +173,14 @@ template <typename T> struct Tap;
 template <> struct Tap<float> {
     static constexpr uint32_t ES = 16;
     using R = float2;
+    using Wt = float2;   // the weight of a pair, as the accumulate takes it
+    __device__ __forceinline__ static Wt weight(float w) { return make_float2(w, w); }
     __device__ __forceinline__ static R row(const unsigned char *e, float2 du2, __half2)
     {
         const float4 q = *reinterpret_cast<const float4 *>(e);   // (taps at c, differences to c + 1)
         return __ffma2_rn(du2, make_float2(q.z, q.w), make_float2(q.x, q.y));
     }
-    __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2 dv2, __half2, float2 W2)
+    __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2 dv2, __half2, Wt W2)
     {
         return __ffma2_rn(W2, lerp2(lo, hi, dv2), acc);
     }
@@ -185,27 +188,43 @@ template <> struct Tap<float> {
 template <> struct Tap<__half> {
     static constexpr uint32_t ES = 8;
     using R = __half2;
+    // FP16 weight (the plan scales w by a power of two that keeps W in range)
+    // for the mixed-precision accumulate below
+    using Wt = unsigned short;
+    __device__ __forceinline__ static Wt weight(float w) { return __half_as_ushort(__float2half_rn(w)); }
     __device__ __forceinline__ static R row(const unsigned char *e, float2, __half2 duh)
     {
         const uint2 q = *reinterpret_cast<const uint2 *>(e);
         const __half2 hx = *reinterpret_cast<const __half2 *>(&q.x), hd = *reinterpret_cast<const __half2 *>(&q.y);
         return __hfma2(duh, hd, hx);
     }
-    __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2, __half2 dvh, float2 W2)
+    // v-lerp in half2, then acc += W r with FP16 inputs and FP32 accumulation,
+    // one rounding (fma.rn.f32.f16)
+    __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2, __half2 dvh, Wt Wh)
     {
-        return __ffma2_rn(W2, __half22float2(__hfma2(dvh, __hsub2(hi, lo), lo)), acc);
+        const __half2 r = __hfma2(dvh, __hsub2(hi, lo), lo);
+        const uint32_t rb = *reinterpret_cast<const uint32_t *>(&r);
+        asm("{\n\t.reg .f16 rl, rh;\n\t"
+            "mov.b32 {rl, rh}, %2;\n\t"
+            "fma.rn.f32.f16 %0, %3, rl, %0;\n\t"
+            "fma.rn.f32.f16 %1, %3, rh, %1;\n\t}"
+            : "+f"(acc.x), "+f"(acc.y)
+            : "r"(rb), "h"(Wh));
+        return acc;
     }
 };
 template <> struct Tap<__nv_bfloat16> {
     static constexpr uint32_t ES = 8;
     using R = float2;
+    using Wt = float2;
+    __device__ __forceinline__ static Wt weight(float w) { return make_float2(w, w); }
     __device__ __forceinline__ static R row(const unsigned char *e, float2 du2, __half2)
     {
         const uint2 q = *reinterpret_cast<const uint2 *>(e);
         return __ffma2_rn(du2, make_float2(__uint_as_float(q.y << 16), __uint_as_float(q.y & 0xffff0000u)),
                           make_float2(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xffff0000u)));
     }
-    __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2 dv2, __half2, float2 W2)
+    __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2 dv2, __half2, Wt W2)
     {
         return __ffma2_rn(W2, lerp2(lo, hi, dv2), acc);
     }
@@ -224,8 +243,8 @@ enum class Reuse { STEP1, STEP2, ANY };
 
 template <typename T, int NV, int L, uint32_t ROWB, uint32_t HB, Reuse MODE>
 __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], const unsigned char *sm,
-                                          uint32_t base, float sig, float vb, float2 du2, __half2 duh, float2 W0,
-                                          float2 W1)
+                                          uint32_t base, float sig, float vb, float2 du2, __half2 duh,
+                                          typename Tap<T>::Wt W0, typename Tap<T>::Wt W1)
 {
     using R = typename Tap<T>::R;
     R lo[NV], hi[NV];
@@ -362,8 +381,8 @@ __global__ void __launch_bounds__(kThreads, NV == 1 ? 3 : 2)
         const int own = s + (NV == 2 ? (t & 1) * a.pair_view_off : 0);
         const float4 *tp = reinterpret_cast<const float4 *>(a.terms + own);
         const float4 t0 = __ldg(tp), t1 = __ldg(tp + 1);
-        const float w0 = __ldg(&a.terms[s].w);
-        const float w1 = NV == 2 ? __ldg(&a.terms[s + a.pair_view_off].w) : 0.0f;
+        const float w0 = __ldg(&a.terms[s].w) * a.wscale;
+        const float w1 = NV == 2 ? __ldg(&a.terms[s + a.pair_view_off].w) * a.wscale : 0.0f;
         // t0 = (A0, A1, A3, B2), t1 = (B3, C0, C1, C3)
         const float ia = (float)i0 - a.cx, ib = ia + (kTileX - 1);
         const float ja = (float)j0 - a.cy, jb = ja + (kTileY - 1);
@@ -439,7 +458,7 @@ __global__ void __launch_bounds__(kThreads, NV == 1 ? 3 : 2)
         float du;
         const uint32_t tu = floor_frac(fmaf(x, f, t2.y), du);
         const float ff = f * f;
-        const float2 W0 = make_float2(t2.x * ff, t2.x * ff), W1 = make_float2(t2.w * ff, t2.w * ff);
+        const typename Tap<T>::Wt W0 = Tap<T>::weight(t2.x * ff), W1 = Tap<T>::weight(t2.w * ff);
         const float sig = t0.w * f;
         const float vb = fmaf(sig, kp0, fmaf(t1.x, f, t2.z));
         // element (n, cu) at offset base + bits(t_v) * ROWB (mod 2^32): n = bits(t_v) - bias,
@@ -479,6 +498,12 @@ __global__ void __launch_bounds__(kThreads, NV == 1 ? 3 : 2)
             }
         }
         return;
+    }
+    if (a.wunscale != 1.0f) {
+#pragma unroll
+        for (int n = 0; n < NV; ++n)
+#pragma unroll
+            for (int p = 0; p < L; ++p) acc[n][p] = make_float2(acc[n][p].x * a.wunscale, acc[n][p].y * a.wunscale);
     }
     if (ci < a.nx && cj < a.ny_cols) {
         write_run<L>(a, k0, ci, cj, acc[0]);
@@ -619,6 +644,8 @@ int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_beg
     a.row0 = p->pk_row0;
     a.cx = (float)((g.nx - 1) / 2.0); a.cy = (float)((g.ny - 1) / 2.0); a.cz = (float)((g.nz - 1) / 2.0);
     a.uc = (float)p->uc; a.vc = (float)p->vc;
+    a.wscale = sizeof(T) == 2 && PkT<T>::TMA == CU_TENSOR_MAP_DATA_TYPE_FLOAT16 ? p->pk_wscale : 1.0f;
+    a.wunscale = 1.0f / a.wscale;
     a.stage_bytes = (uint32_t)b.stage_bytes;
     a.box_tx_bytes = (uint32_t)((size_t)b.box_h * NV * BW * 4 * es);
     void (*kern)(const PkArgs, const CUtensorMap) = bp_packed_kernel<T, NV, BW, pk_pairs(NV)>;
@@ -674,6 +701,17 @@ void plan_packed(ifdk_plan_s *p)
     p->pk_row0 = std::min(0, p->two_vc - (p->g.nv - 1));
     p->pk_rows = p->fold_ok ? (int)std::floor(p->vc) + 3 - p->pk_row0 : 0;
     p->pk_nu = (p->g.nu + 2) / 2 * 2;   // columns -1 .. nu - 1, rounded up to even
+    // FP16 weights: W = w_s f^2 <= max w_s / z_min^2 with z_min >= d - r_xy (r_xy the
+    // largest voxel distance from the axis); scale by 2^k so that it lies in [1, 2)
+    {
+        const ifdk_geometry &g = p->g;
+        const double hx = 0.5 * (g.nx - 1) * g.dx, hy = 0.5 * (g.ny - 1) * g.dy;
+        const double zmin = g.sid - std::sqrt(hx * hx + hy * hy);
+        double wmax = 0.0;
+        for (const ViewTerms &t : p->terms) wmax = std::max(wmax, (double)std::fabs(t.w));
+        const double Wmax = wmax / (zmin * zmin);
+        p->pk_wscale = Wmax > 0.0 ? (float)std::ldexp(1.0, -(int)std::floor(std::log2(Wmax))) : 1.0f;
+    }
     for (int t = 0; t < 3; ++t) {
         p->pk[t] = size_packed(p, t, 1);
         p->pk2[t] = p->pk[t].path ? size_packed(p, t, 2) : PkLaunch{};

@@ -92,6 +92,7 @@ struct ifdk_plan_s {
     // packed views: rows r in [pk_row0, pk_row0 + pk_rows) pair row r with row 2 vc - r; a row
     // holds pk_nu elements (columns -1 .. nu - 1, rounded up to even) of 4 values each
     int pk_rows = 0, pk_nu = 0, pk_row0 = 0;   // pk_row0: detector row of packed row 0 (<= 0)
+    float pk_wscale = 1.0f;              // power of two putting the largest FP16 weight in [1, 2)
     ifdk::PkLaunch pk[3], pk2[3];        // per storage type: single views / half-turn view pairs
     bool half_turn = false;              // view s + np/2 is view s turned by pi (exactly)
     bool use_half_turn = true;           // caller switch (ifdk_set_view_pairing)
