@@ -241,6 +241,7 @@ __device__ __forceinline__ ColView col_view(uint32_t vs, const Block &b)
 __device__ __forceinline__ void write_run(const BpArgs &a, const Block &b, const float2 *acc)
 {
     constexpr int L = kPairs;
+    static_assert(L % 4 == 0, "the vector path stores float4 runs from k0 = a multiple of L");
     if (b.i >= a.nx || b.j >= a.ny) return;
     float *col = a.vol + ((size_t)b.i * a.ny + b.j) * (size_t)a.nz;
     const int half = a.nz / 2, npairs = (a.nz + 1) / 2;

@@ -84,14 +84,17 @@ struct PkArgs {
 
 template <typename T> struct PkT;
 template <> struct PkT<float> {
+    static constexpr int CODE = IFDK_F32;
     static constexpr int ALIGN = 1;
     static constexpr CUtensorMapDataType TMA = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
 };
 template <> struct PkT<__half> {
+    static constexpr int CODE = IFDK_F16;
     static constexpr int ALIGN = 2;
     static constexpr CUtensorMapDataType TMA = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
 };
 template <> struct PkT<__nv_bfloat16> {
+    static constexpr int CODE = IFDK_BF16;
     static constexpr int ALIGN = 2;
     static constexpr CUtensorMapDataType TMA = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
 };
@@ -300,6 +303,7 @@ __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], cons
 template <int L>
 __device__ __forceinline__ void write_run(const PkArgs &a, int k0, int i, int j, const float2 *acc)
 {
+    static_assert(L % 4 == 0, "the vector path stores float4 runs from k0 = a multiple of L");
     float *col = a.vol + ((size_t)i * a.ny + j) * (size_t)a.nz;
     const int half = a.nz / 2, npairs = (a.nz + 1) / 2;
     if ((a.nz & 3) == 0 && k0 + L <= half) {
@@ -336,7 +340,7 @@ constexpr uint32_t kPkFull = 0, kPkEmpty = 64, kPkAbort = 128, kPkLast = 160, kP
 static_assert(kPkMaxStages * 8 <= 64 && kPkLast + 4 * kPkMaxStages <= kPkStage0, "shared-memory map");
 
 template <typename T, int NV, int BW, int L>
-__global__ void __launch_bounds__(kThreads, NV == 1 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, pk_blocks(NV))
     bp_packed_kernel(const PkArgs a, const __grid_constant__ CUtensorMap tmap)
 {
     constexpr uint32_t ES = Tap<T>::ES;
@@ -561,7 +565,7 @@ PkLaunch size_packed(const ifdk_plan_s *p, int q_dtype, int nv)
     b.align = q_dtype == IFDK_F32 ? 1 : 2;
     const int ny_cols = nv == 2 ? g.ny / 2 : g.ny;
     const int tiles_x = (g.nx + kTileX - 1) / kTileX, tiles_y = (ny_cols + kTileY - 1) / kTileY;
-    const int L = pk_pairs(nv), npairs = (g.nz + 1) / 2, zblocks = (npairs + L - 1) / L;
+    const int L = pk_pairs(nv, q_dtype), npairs = (g.nz + 1) / 2, zblocks = (npairs + L - 1) / L;
     b.grid_x = tiles_x * tiles_y;
     b.grid_y = zblocks;
     if (!p->fold_ok) return b;
@@ -585,8 +589,9 @@ PkLaunch size_packed(const ifdk_plan_s *p, int q_dtype, int nv)
     if (need > kPkBoxL || b.box_h > 256) return b;
     const size_t box = (size_t)b.box_h * nv * b.bw * 4 * es;
     b.stage_bytes = (kPkBox + box + 127) / 128 * 128;
-    // as many stages as keep 3 (nv = 1) or 2 (nv = 2) blocks per SM, at most 8
-    const size_t budget = nv == 1 ? 74 * 1024 : 112 * 1024;
+    // as many stages as keep pk_blocks(nv) blocks per SM (228 KiB of shared
+    // memory per SM, 1 KiB of it reserved per block), at most kPkMaxStages
+    const size_t budget = 228 * 1024 / pk_blocks(nv) - 1024;
     b.stages = (int)std::min<size_t>(kPkMaxStages, (budget - 128 - kPkStage0) / b.stage_bytes);
     if (b.stages < 3) b.stages = 3;   // fewer blocks per SM rather than a shallower ring
     b.smem = 128 + kPkStage0 + (size_t)b.stages * b.stage_bytes;
@@ -648,7 +653,7 @@ int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_beg
     a.wunscale = 1.0f / a.wscale;
     a.stage_bytes = (uint32_t)b.stage_bytes;
     a.box_tx_bytes = (uint32_t)((size_t)b.box_h * NV * BW * 4 * es);
-    void (*kern)(const PkArgs, const CUtensorMap) = bp_packed_kernel<T, NV, BW, pk_pairs(NV)>;
+    void (*kern)(const PkArgs, const CUtensorMap) = bp_packed_kernel<T, NV, BW, pk_pairs(NV, PkT<T>::CODE)>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem) != cudaSuccess)
         return IFDK_ERR_CUDA;
     kern<<<dim3(b.grid_x, b.grid_y), kThreads, b.smem, stream>>>(a, tmap);

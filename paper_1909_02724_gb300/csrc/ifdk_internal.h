@@ -48,8 +48,12 @@ struct BpLaunch {
 // of TMA stages of one view group each.
 constexpr int kPkMaxStages = 8;
 constexpr int kPkBoxS = 32, kPkBoxL = 48;   // box widths (elements) the kernel is built for
-// z pairs per thread: 16 for single views, 12 with half-turn view pairs (two columns' runs)
-constexpr int pk_pairs(int nv) { return nv == 2 ? 12 : 16; }
+// z pairs per thread: 16 for single views; with half-turn view pairs (two
+// columns' runs in registers) 16 for FP16 storage and 12 for FP32 / BF16,
+// whose wider taps need the registers.  A multiple of 4 (vector writes).
+constexpr int pk_pairs(int nv, int q_dtype) { return nv == 2 && q_dtype != IFDK_F16 ? 12 : 16; }
+// resident blocks per SM the packed kernel is built for (registers) and sized for (shared memory)
+constexpr int pk_blocks(int nv) { return nv == 2 ? 2 : 3; }
 
 struct PkLaunch {
     int path;          // 1 = packed mirror-pair kernel applies, 0 = not
