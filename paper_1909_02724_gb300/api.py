@@ -57,3 +57,50 @@ def fdk_host(plan: Plan, E_host: torch.Tensor, vol_host: torch.Tensor, E_dev: to
         vol_host.copy_(vol_dev, non_blocking=True)
     s.synchronize()
     return vol_host
+
+
+def fdk_host_pipeline(plan: Plan, E_host: torch.Tensor, vol_host: torch.Tensor, E_dev: list, Q_dev: torch.Tensor,
+                      vol_dev: list, Qp_dev: torch.Tensor | None = None, n_steps: int = 1,
+                      split_terms: int | None = None) -> torch.Tensor:
+    """n_steps FDK reconstructions from host projections to a host volume with the
+    copies of one step overlapping the computation of its neighbours.
+
+    Every step copies E_host in (pinned) and its volume out to vol_host; E_dev
+    and vol_dev are two device buffers each (double buffering), Q_dev / Qp_dev
+    one.  Streams: host-to-device copies, computation (filter, pack,
+    back-projection) and device-to-host copies, ordered by events so that a
+    buffer is refilled only after the step that used it has finished with it.
+    Returns once the last volume is in vol_host."""
+    dev = E_dev[0].device
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    s_c = torch.cuda.current_stream(dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    filtered = [torch.cuda.Event() for _ in range(2)]
+    computed = [torch.cuda.Event() for _ in range(2)]
+    drained = [torch.cuda.Event() for _ in range(2)]
+    for k in range(n_steps):
+        b = k & 1
+        with torch.cuda.stream(s_in):
+            if k >= 2:
+                s_in.wait_event(filtered[b])               # step k-2's filter has read E_dev[b]
+            E_dev[b].copy_(E_host, non_blocking=True)
+            copied[b].record(s_in)
+        s_c.wait_event(copied[b])
+        if k >= 2:
+            s_c.wait_event(drained[b])                     # step k-2's volume has left vol_dev[b]
+        vol_dev[b].zero_()
+        plan.filter(E_dev[b], Q_dev, split_terms=split_terms, stream=s_c)
+        filtered[b].record(s_c)
+        if Qp_dev is not None:
+            plan.pack(Q_dev, Qp_dev, stream=s_c)
+            plan.backproject_packed(Qp_dev, vol_dev[b], stream=s_c)
+        else:
+            plan.backproject(Q_dev, vol_dev[b], stream=s_c)
+        computed[b].record(s_c)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(computed[b])
+            vol_host.copy_(vol_dev[b], non_blocking=True)
+            drained[b].record(s_out)
+    s_out.synchronize()
+    s_c.synchronize()
+    return vol_host

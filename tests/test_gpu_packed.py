@@ -210,3 +210,24 @@ def test_packed_path_refuses_what_it_does_not_cover():
         B.ifdk_backproject_packed(p2.handle, raw.data_ptr() + 4, B.IFDK_F32, 0, g2.np, v2)
     assert e.value.code == B.IFDK_ERR_ALIGNMENT
     assert float(v2.abs().max()) == 0.0
+
+
+def test_fdk_host_pipeline_matches_device_fdk():
+    """The pipelined host-to-host FDK (copies of one step overlapping its
+    neighbours' computation) returns the device FDK's volume."""
+    from paper_1909_02724_gb300.api import fdk, fdk_host_pipeline
+    g = GEOMS["ragged"]
+    E = torch.from_numpy(phantom_E(g)).cuda()
+    p = B.Plan(g)
+    ref = fdk(p, E)
+    E_host = E.cpu().pin_memory()
+    vol_host = torch.empty((g.nx, g.ny, g.nz), pin_memory=True)
+    E2 = [torch.empty_like(E), torch.empty_like(E)]
+    vol2 = [torch.empty_like(ref), torch.empty_like(ref)]
+    Q = torch.empty_like(E)
+    Qp = torch.empty(p.packed_shape(torch.float32), device="cuda")
+    for n in (1, 3):
+        vol_host.zero_()
+        fdk_host_pipeline(p, E_host, vol_host, E2, Q, vol2, Qp_dev=Qp, n_steps=n)
+        assert torch.equal(vol_host, ref.cpu())
+    assert p.device_status() == 0
