@@ -277,10 +277,12 @@ def run_ours(args):
     value = world * g.updates * args.steps / (ms * 1e-3) / 2 ** 30
 
     # launches of our kernels per step: tensor-core filter (a split pre-pass and a GEMM per
-    # chunk of up to 16384 rows, the preferred workspace), the pack (packed path) and
-    # one back-projection (the full scan pairs up, or is one range of single views)
+    # chunk of rows that fits the preferred workspace), the pack (packed path) and one
+    # back-projection (the full scan pairs up, or is one range of single views)
     rows = g.np * g.nv
-    cap = min(16384, -(-rows // 128) * 128)
+    terms = 3 if tdt == torch.float32 else 2
+    ws_min, ws_pref = B.ifdk_filter_workspace_size(plan.handle, terms)
+    cap = ws_pref // (ws_min // 128)
     launches = (2 * -(-rows // cap) + (2 if packed else 1)) * args.steps
 
     # end to end through host buffers (pinned), copies inside the timed region: every

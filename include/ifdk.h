@@ -115,8 +115,8 @@ int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_ter
                 void *workspace, size_t workspace_bytes, void *stream);
 
 /* Workspace of ifdk_filter for split_terms: the minimum (one 128-row tile of
-   split operands) and a preferred size (up to 16384 rows per launch).  Either
-   pointer may be NULL.  0 bytes for split_terms = 0. */
+   split operands) and a preferred size (every row in one launch, up to 1 GiB).
+   Either pointer may be NULL.  0 bytes for split_terms = 0. */
 int ifdk_filter_workspace_size(ifdk_plan p, int split_terms, size_t *min_bytes,
                                size_t *preferred_bytes);
 

@@ -21,10 +21,13 @@
 //
 // Kernels: a pre-pass writes d of a chunk of rows as s BF16 planes into a
 // caller-provided workspace; the GEMM kernel computes one 128 x 128 output
-// tile per block: one lane streams A / B tiles by TMA (128-byte swizzle)
-// through a 4-stage mbarrier ring, one lane issues tcgen05.mma (M = 128,
-// N = 128, K = 16) into four TMEM accumulators (see acc_of), and the four
-// warps read them back (tcgen05.ld), add them and store the storage type.
+// tile per block: one lane streams, per K block of 64, all s data planes and
+// all s tap planes by TMA (128-byte swizzle) into one stage of an mbarrier
+// ring, so every plane is read once per K block whatever the number of term
+// products; one lane issues tcgen05.mma (M = 128, N = 128, K = 16) for every
+// term pair of the stage into four TMEM accumulators (see acc_of), and the
+// four warps read them back (tcgen05.ld), add them and store the storage
+// type.
 #include <cstring>
 
 #include "ifdk_device.cuh"
@@ -34,11 +37,13 @@ namespace ifdk {
 namespace {
 
 constexpr int kTcM = 128, kTcN = 128, kTcK = 64;
-constexpr int kTcStages = 4;
 constexpr int kTcThreads = 128;
-constexpr uint32_t kTileA = kTcM * kTcK * 2, kTileB = kTcN * kTcK * 2;   // 16 KiB each
-constexpr uint32_t kTcSmemBars = kTcStages * (kTileA + kTileB);          // after the tiles
-constexpr size_t kTcSmem = 1024 + kTcSmemBars + 256;
+constexpr uint32_t kTileA = kTcM * kTcK * 2, kTileB = kTcN * kTcK * 2;   // 16 KiB each (one plane)
+constexpr int kTcMaxStages = 6;
+// stages of s data planes + s tap planes (32 KiB per plane pair) within 192 KiB
+constexpr int tc_stages(int planes) { return planes == 3 ? 2 : (planes == 2 ? 3 : 6); }
+constexpr uint32_t tc_stage_bytes(int planes) { return (uint32_t)planes * (kTileA + kTileB); }
+constexpr size_t tc_smem(int planes) { return 1024 + (size_t)tc_stages(planes) * tc_stage_bytes(planes) + 256; }
 constexpr int kAccs = 4;
 constexpr uint32_t kTmemCols = kAccs * kTcN;   // four FP32 accumulators of kTcN columns
 
@@ -57,6 +62,7 @@ struct TcArgs {
     long long row0;       // first output row of this chunk
     int nrows;            // rows in this chunk
     int nu, nk, npairs;   // K blocks of 64, term pairs
+    int planes, stages;   // split terms (planes of each operand per stage), ring depth
 };
 
 // Term pairs (data i, tap j): s = 1, 2, 3 use the first 1, 3, 6.
@@ -115,17 +121,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     const uint32_t sbase = smem_addr(smem_dyn);
     const uint32_t s0 = sbase + ((1024u - (sbase & 1023u)) & 1023u);   // 128-byte swizzle wants 1 KiB alignment
-    const uint32_t tilesA = s0, tilesB = s0 + kTcStages * kTileA;
-    const uint32_t full = s0 + kTcSmemBars, empty = full + 8 * kTcStages, accum = empty + 8 * kTcStages;
+    const int S = a.stages;
+    const uint32_t stage_bytes = (uint32_t)a.planes * (kTileA + kTileB);
+    // stage s: data planes at s0 + s * stage_bytes, then the tap planes
+    const uint32_t full = s0 + (uint32_t)S * stage_bytes, empty = full + 8 * kTcMaxStages,
+                   accum = empty + 8 * kTcMaxStages;
     const uint32_t tslot = accum + 8, abort_flag = tslot + 4;   // abort_flag + 4: accumulators written
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m_tile = blockIdx.x, n_tile = blockIdx.y;
-    const int units = a.nk * a.npairs;
+    const int units = a.nk;   // one unit = one K block, all planes of both operands
 
     if (tid == 0) {
         prefetch_tmap(&tmA);
         prefetch_tmap(&tmB);
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(full + 8 * s, 1);
             mbar_init(empty + 8 * s, 1);
         }
@@ -141,38 +150,43 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(tslot) : "memory");
 
     if (warp == 0 && lane == 0) {
-        // TMA producer: unit u = (K block u / npairs, term pair) into stage u % S
+        // TMA producer: K block u (every data plane, every tap plane) into stage u % S
         for (int u = 0; u < units; ++u) {
-            const int s = u % kTcStages;
-            if (!mbar_wait_bounded(empty + 8 * s, ((u / kTcStages) & 1) ^ 1, a.wait_ns)) {
+            const int s = u % S;
+            if (!mbar_wait_bounded(empty + 8 * s, ((u / S) & 1) ^ 1, a.wait_ns)) {
                 asm volatile("st.shared.u32 [%0], %1;" ::"r"(abort_flag), "r"(1u) : "memory");
                 break;
             }
-            int ti, tj;
-            term_pair(u % a.npairs, ti, tj);
-            const int kb = u / a.npairs;
-            mbar_arrive_expect_tx(full + 8 * s, kTileA + kTileB);
-            tma_load_3d(tilesA + s * kTileA, &tmA, kb * kTcK, m_tile * kTcM, ti, full + 8 * s);
-            tma_load_3d(tilesB + s * kTileB, &tmB, kb * kTcK, n_tile * kTcN, tj, full + 8 * s);
+            const uint32_t st = s0 + (uint32_t)s * stage_bytes;
+            mbar_arrive_expect_tx(full + 8 * s, stage_bytes);
+            tma_load_3d(st, &tmA, u * kTcK, m_tile * kTcM, 0, full + 8 * s);
+            tma_load_3d(st + (uint32_t)a.planes * kTileA, &tmB, u * kTcK, n_tile * kTcN, 0, full + 8 * s);
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: 4 x (M128 N128 K16) per unit into TMEM accumulator acc_of(kb, q)
+        // MMA issuer: per term pair (i, j) of a K block, 4 x (M128 N128 K16) of data
+        // plane i and tap plane j into TMEM accumulator acc_of(kb, q)
         constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, kTcN);
         uint32_t started = 0;   // bit c: accumulator c has been written
         for (int u = 0; u < units; ++u) {
-            const int s = u % kTcStages;
-            if (!mbar_wait_bounded(full + 8 * s, (u / kTcStages) & 1, a.wait_ns)) {
+            const int s = u % S;
+            if (!mbar_wait_bounded(full + 8 * s, (u / S) & 1, a.wait_ns)) {
                 asm volatile("st.shared.u32 [%0], %1;" ::"r"(abort_flag), "r"(1u) : "memory");
                 break;
             }
             tc::fence_after();
-            const int c = acc_of(u / a.npairs, u % a.npairs);
-            const uint32_t d = tmem + (uint32_t)c * kTcN;
-            const uint64_t da = tc::desc_sw128(tilesA + s * kTileA), db = tc::desc_sw128(tilesB + s * kTileB);
+            const uint32_t st = s0 + (uint32_t)s * stage_bytes;
+            for (int q = 0; q < a.npairs; ++q) {
+                int ti, tj;
+                term_pair(q, ti, tj);
+                const int c = acc_of(u, q);
+                const uint32_t d = tmem + (uint32_t)c * kTcN;
+                const uint64_t da = tc::desc_sw128(st + (uint32_t)ti * kTileA);
+                const uint64_t db = tc::desc_sw128(st + (uint32_t)a.planes * kTileA + (uint32_t)tj * kTileB);
 #pragma unroll
-            for (int kk = 0; kk < kTcK / 16; ++kk) {   // +32 bytes along K = +2 in the address field
-                tc::mma_f16(d, da + 2 * kk, db + 2 * kk, idesc, (started >> c) & 1u);
-                started |= 1u << c;
+                for (int kk = 0; kk < kTcK / 16; ++kk) {   // +32 bytes along K = +2 in the address field
+                    tc::mma_f16(d, da + 2 * kk, db + 2 * kk, idesc, (started >> c) & 1u);
+                    started |= 1u << c;
+                }
             }
             tc::commit(empty + 8 * s);
         }
@@ -293,13 +307,16 @@ double bf2d(uint16_t b)
     return f;
 }
 
-int encode_bf16_3d(CUtensorMap *m, const void *base, uint64_t kpad, uint64_t rows, uint64_t planes, uint32_t box_rows)
+// 3-D map [planes][rows][kpad] of BF16 whose box is box_planes planes of
+// box_rows x 64 (the planes land one after another in shared memory).
+int encode_bf16_3d(CUtensorMap *m, const void *base, uint64_t kpad, uint64_t rows, uint64_t planes, uint32_t box_rows,
+                   uint32_t box_planes)
 {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return IFDK_ERR_CUDA;
     const cuuint64_t dims[3] = {kpad, rows, planes};
     const cuuint64_t strides[2] = {kpad * 2, kpad * rows * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)kTcK, box_rows, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)kTcK, box_rows, box_planes};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -322,11 +339,13 @@ int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size
     if (cap < kTcM) return IFDK_ERR_INVALID;
     if (cap > rows) cap = (rows + kTcM - 1) / kTcM * kTcM;
     if (cap > 65535LL * kTcM) cap = 65535LL * kTcM;
-    CUtensorMap tmA;
-    int rc = encode_bf16_3d(&tmA, ws, kpad, (uint64_t)cap, planes, kTcM);
+    CUtensorMap tmA, tmB;
+    int rc = encode_bf16_3d(&tmA, ws, kpad, (uint64_t)cap, planes, kTcM, planes);
+    if (rc == IFDK_OK) rc = encode_bf16_3d(&tmB, p->d_tsplit, kpad, npad, 3, kTcN, planes);
     if (rc != IFDK_OK) return rc;
     auto kern = filter_tc_kernel<TQ>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) != cudaSuccess)
+    const size_t smem = tc_smem(planes);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return IFDK_ERR_CUDA;
     TcArgs a;
     a.Q = Q;
@@ -335,6 +354,8 @@ int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size
     a.nu = g.nu;
     a.nk = kpad / kTcK;
     a.npairs = terms == 3 ? 6 : (terms == 2 ? 3 : 1);
+    a.planes = planes;
+    a.stages = tc_stages(planes);
     for (long long r0 = 0; r0 < rows; r0 += cap) {
         const int nr = (int)(rows - r0 < cap ? rows - r0 : cap);
         const long long threads = (long long)nr * (kpad / 8);
@@ -343,7 +364,7 @@ int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size
             cap * kpad);
         a.row0 = r0;
         a.nrows = nr;
-        kern<<<dim3((nr + kTcM - 1) / kTcM, npad / kTcN), kTcThreads, kTcSmem, stream>>>(tmA, p->tc_tmap_b, a);
+        kern<<<dim3((nr + kTcM - 1) / kTcM, npad / kTcN), kTcThreads, smem, stream>>>(tmA, tmB, a);
         if (cudaGetLastError() != cudaSuccess) return IFDK_ERR_CUDA;
     }
     return IFDK_OK;
@@ -378,7 +399,7 @@ int plan_filter_tc(ifdk_plan_s *p)
         }
     if (cudaMalloc(&p->d_tsplit, t.size() * 2) != cudaSuccess) return IFDK_ERR_NOMEM;
     if (cudaMemcpy(p->d_tsplit, t.data(), t.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return IFDK_ERR_CUDA;
-    return encode_bf16_3d(&p->tc_tmap_b, p->d_tsplit, p->tc_kpad, p->tc_npad, 3, kTcN);
+    return IFDK_OK;
 }
 
 size_t filter_workspace_min(const ifdk_plan_s *p, int terms)

@@ -104,7 +104,6 @@ struct ifdk_plan_s {
     // tensor-core filter: Toeplitz matrix as 3 BF16 planes [3][tc_npad][tc_kpad]
     int tc_kpad = 0, tc_npad = 0;
     uint16_t *d_tsplit = nullptr;
-    CUtensorMap tc_tmap_b;
     // host streaming (ifdk_backproject_host): copy stream and, per staging
     // half, "copy landed" and "back-projection done" events
     cudaStream_t copy_stream = nullptr;

@@ -254,7 +254,9 @@ int ifdk_filter_workspace_size(ifdk_plan p, int split_terms, size_t *min_bytes, 
     if (!p || split_terms < 0 || split_terms > 3) return IFDK_ERR_INVALID;
     const size_t mn = split_terms ? filter_workspace_min(p, split_terms) : 0;
     const long long rows = (long long)p->g.np * p->g.nv;
-    const long long pref_rows = rows < 16384 ? (rows + 127) / 128 * 128 : 16384;
+    // preferred: every row in one launch, up to 1 GiB of split operands
+    long long pref_rows = (rows + 127) / 128 * 128;
+    if (mn && pref_rows * (long long)(mn / 128) > (1LL << 30)) pref_rows = std::max(128LL, (1LL << 30) / (long long)(mn / 128) / 128 * 128);
     if (min_bytes) *min_bytes = mn;
     if (preferred_bytes) *preferred_bytes = split_terms ? mn / 128 * (size_t)pref_rows : 0;
     return IFDK_OK;
