@@ -215,6 +215,7 @@ def run_ours(args):
     from paper_1909_02724_gb300.api import fdk_host, fdk_host_pipeline
     from paper_1909_02724_gb300.build import build
     from paper_1909_02724_gb300.geometry import gups
+    from paper_1909_02724_gb300.parallel import max_over_ranks
     from paper_1909_02724_gb300.phantom import workload, workload_projections_gpu
 
     build()
@@ -269,10 +270,7 @@ def run_ours(args):
     ck = clocks.stop()
     ms = t0.elapsed_time(t1)
     bp_ms = float(np.mean([a.elapsed_time(b) for a, b in bp_events]))
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks(ms, device=dev)
     ms_per_step = ms / args.steps
     value = world * g.updates * args.steps / (ms * 1e-3) / 2 ** 30
 
@@ -303,10 +301,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         a = time.perf_counter()
         fdk_host_pipeline(plan, E_host, vol_host, E2, Q, vol2, Qp_dev=Qp, n_steps=e_steps)
-        e_s = torch.tensor([time.perf_counter() - a], device=dev)
-        if world > 1:
-            dist.all_reduce(e_s, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * g.updates * e_steps / float(e_s.item()) / 2 ** 30, "unit": UNIT,
+        e_s = max_over_ranks(time.perf_counter() - a, device=dev)
+        e2e = {"value": world * g.updates * e_steps / e_s / 2 ** 30, "unit": UNIT,
                "h2d_bytes_per_step": E.numel() * 4, "d2h_bytes_per_step": vol.numel() * 4,
                "steps": e_steps, "overlap": "copies of step k overlap compute of steps k-1, k+1"}
         del E2[1], vol2[1]

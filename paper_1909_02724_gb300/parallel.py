@@ -1,0 +1,104 @@
+"""Work decomposition over ranks (Sec. 4 of the iFDK paper), host side.
+
+The paper splits an FDK reconstruction over an R x C grid of workers:
+columns split the views (each column back-projects Np / C views into a
+partial volume, and the partial volumes are summed, the paper's MPI_Reduce),
+rows split the volume into z-slabs (each row back-projects every view into
+its own slab; slabs and their z-mirrors are independent, no collective).
+This module computes those partitions and the two collectives they need,
+through torch.distributed (NCCL for GPU tensors, gloo for CPU tensors).  The
+back-projection itself stays in the CUDA library: a view shard is a call with
+[view_begin, view_begin + view_count), a slab shard a plan of the slab's
+geometry (vol_off_z = the slab centre's world Z; the general kernel serves
+off-centre slabs, a centred slab keeps the mirror paths).
+
+bench.py runs independent problems per rank (weak scaling, no data-path
+collective) and uses max_over_ranks for its timing.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+from .geometry import Geometry
+
+
+def split_range(n: int, parts: int, index: int) -> tuple[int, int]:
+    """[begin, end) of part `index` of `parts` near-equal contiguous parts of
+    range(n) (the first n % parts parts are one longer)."""
+    if parts < 1 or not 0 <= index < parts or n < 0:
+        raise ValueError("bad partition")
+    q, r = divmod(n, parts)
+    begin = index * q + min(index, r)
+    return begin, begin + q + (1 if index < r else 0)
+
+
+def view_shard(geom: Geometry, world: int, rank: int) -> tuple[int, int]:
+    """The views a column worker back-projects: (view_begin, view_count)."""
+    b, e = split_range(geom.np, world, rank)
+    return b, e - b
+
+
+@dataclass
+class Slab:
+    k_begin: int      # first voxel index k of the slab in the whole volume
+    k_count: int
+    geom: Geometry    # the slab as a volume of its own (centre shifted along Z)
+
+
+def slab_shard(geom: Geometry, world: int, rank: int) -> Slab:
+    """The z-slab a row worker reconstructs.  Voxel k of the slab is voxel
+    k_begin + k of the whole volume: its world Z, -dz (k_begin + k - (nz-1)/2)
+    + vol_off_z (the index flip of M0 in Eq. 2), is the slab's own
+    -dz (k - (k_count-1)/2) + slab_off_z with the offset below."""
+    b, e = split_range(geom.nz, world, rank)
+    n = e - b
+    off = geom.vol_off_z - geom.dz * (b + (n - 1) / 2.0 - (geom.nz - 1) / 2.0)
+    return Slab(b, n, geom.with_(nz=n, vol_off_z=off))
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """max of a host scalar over the ranks of the default process group
+    (the scalar itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_volume(vol, dst: int = 0):
+    """Sums the partial volumes of a view split onto rank dst (the paper's
+    MPI_Reduce of the column workers' sub-volumes), in place on dst."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.reduce(vol, dst=dst, op=dist.ReduceOp.SUM)
+    return vol
+
+
+def gather_slabs(slab_vol, full_vol=None, dst: int = 0, nz: int | None = None):
+    """Collects the slabs of a row split on rank dst into full_vol [nx][ny][nz]
+    (k fastest), slab r holding k in split_range(nz, world, r)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        if full_vol is not None:
+            full_vol.copy_(slab_vol)
+            return full_vol
+        return slab_vol
+    world, rank = dist.get_world_size(), dist.get_rank()
+    nz = full_vol.shape[2] if full_vol is not None else nz
+    # gather wants equal shapes: every slab travels padded to the longest one
+    kmax = split_range(nz, world, 0)[1]
+    send = torch.zeros(slab_vol.shape[:2] + (kmax,), dtype=slab_vol.dtype, device=slab_vol.device)
+    send[:, :, :slab_vol.shape[2]] = slab_vol
+    if rank == dst:
+        parts = [torch.empty_like(send) for _ in range(world)]
+        dist.gather(send, gather_list=parts, dst=dst)
+        for r in range(world):
+            b, e = split_range(nz, world, r)
+            full_vol[:, :, b:e] = parts[r][:, :, :e - b]
+    else:
+        dist.gather(send, dst=dst)
+    return full_vol
