@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-view-pairing", action="store_true",
                     help="back-project every view singly (no half-turn view pairs)")
+    ap.add_argument("--view-split", type=int, default=0,
+                    help="cap on the view split of small volumes (0 automatic, 1 off)")
     ap.add_argument("--standard", action="store_true",
                     help="back-project the filtered views as filtered (ifdk_backproject), not packed")
     return ap.parse_args()
@@ -224,7 +226,9 @@ def run_ours(args):
     tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.dtype]
     plan = B.Plan(g)
     plan.set_view_pairing(not args.no_view_pairing)
+    plan.set_view_split(args.view_split)
     packed = not args.standard and plan.has_packed(tdt)
+    splits = plan.view_split(tdt) if packed else 1
     info = plan.packed_info(tdt) if packed else plan.info(tdt)
     dev = torch.device("cuda", local)
     E = workload_projections_gpu(w)
@@ -274,14 +278,30 @@ def run_ours(args):
     ms_per_step = ms / args.steps
     value = world * g.updates * args.steps / (ms * 1e-3) / 2 ** 30
 
+    # output stage (Algorithm 4's reshape: k-fastest volume -> i-fastest slices), not part
+    # of the step; timed alone on the step's volume (512 MiB in, 512 MiB out: above L2)
+    slices = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        plan.slices(vol, slices)
+    sl_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+    for a, b in sl_events:
+        a.record(stream)
+        plan.slices(vol, slices)
+        b.record(stream)
+    torch.cuda.synchronize()
+    sl_ms = float(np.mean([a.elapsed_time(b) for a, b in sl_events]))
+    sl_bytes = 8 * g.nx * g.ny * g.nz
+    del slices
+
     # launches of our kernels per step: tensor-core filter (a split pre-pass and a GEMM per
     # chunk of rows that fits the preferred workspace), the pack (packed path) and one
-    # back-projection (the full scan pairs up, or is one range of single views)
+    # back-projection (the full scan pairs up, or is one range of single views), plus the
+    # sum of the partial volumes when a small volume splits its views
     rows = g.np * g.nv
     terms = 3 if tdt == torch.float32 else 2
     ws_min, ws_pref = B.ifdk_filter_workspace_size(plan.handle, terms)
     cap = ws_pref // (ws_min // 128)
-    launches = (2 * -(-rows // cap) + (2 if packed else 1)) * args.steps
+    launches = (2 * -(-rows // cap) + (2 if packed else 1) + (1 if splits > 1 else 0)) * args.steps
 
     # end to end through host buffers (pinned), copies inside the timed region: every
     # step copies its projections in and its volume out; the copies of one step
@@ -333,6 +353,13 @@ def run_ours(args):
                                           if ck.get("sm_mhz") else None),
                 "bp_ms_per_launch": bp_ms}
 
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    output_stage = {"kernel": "slices_kernel<float>", "ms_per_launch": sl_ms,
+                    "bytes_per_launch": sl_bytes, "achieved": sl_bytes / (sl_ms * 1e-3) / 1e9,
+                    "peak": hbm, "unit": "GB/s", "bound": "hbm",
+                    "frac": sl_bytes / (sl_ms * 1e-3) / 1e9 / hbm,
+                    "peak_basis": "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
+
     cpu = None
     if not args.no_cpu and world == 1:
         cpu = cpu_baseline(w, E, vol, plan, Q)
@@ -345,9 +372,9 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (E, Q, vol each >= 256 MiB)",
                        "bp_path": ("packed views" + (", half-turn view pairs" if info["path"] == 2 else ""))
                        if packed else "filtered views as stored",
-                       "bp_launch": info},
+                       "bp_launch": info, "view_split": splits},
             "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roofline,
-            "cpu_baseline": cpu}
+            "cpu_baseline": cpu, "output_stage": output_stage}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

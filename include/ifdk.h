@@ -271,6 +271,25 @@ int ifdk_backproject_host(ifdk_plan p, const void *Q_host, int q_dtype, int host
                           int view_begin, int view_count, int chunk_views, void *staging,
                           size_t staging_bytes, float *vol, void *stream);
 
+/* View split of the packed back-projection for small volumes.  Throughput
+   falls as the volume shrinks against its input (the alpha of Table 5).
+   A small volume has too few columns and z-runs to fill the GPU: its grid
+   covers at most half a wave.  For such volumes (up to 64 MiB of partial
+   volumes, allocated by ifdk_create) ifdk_backproject_packed splits the view
+   range of each launch into S parts, one per grid layer.  S fills about one
+   wave; each part holds at least 2 views or view pairs, and S <= 16.  Each
+   part's sums are stored in a partial volume of the plan.  A second kernel
+   then adds the parts to vol in part order, so results are reproducible but
+   round differently from S = 1.  Launches that split share the plan's
+   partial volumes: calls on one plan must not overlap on different streams
+   while a split is in use.
+   ifdk_set_view_split caps S: 0 = automatic (default), 1 = never split,
+   n >= 2 = at most n.  Returns IFDK_ERR_INVALID for a negative cap.
+   ifdk_view_split returns in *splits the S that a packed back-projection of
+   all np views of q_dtype uses on this plan (1: no split). */
+int ifdk_set_view_split(ifdk_plan p, int max_splits);
+int ifdk_view_split(ifdk_plan p, int q_dtype, int *splits);
+
 /* Exact adjoint of ifdk_backproject (FP32): for every voxel, view in the
    range and bilinear tap, P[s][tap] += w_s f^2 (bilinear weight) vol[i][j][k].
    It is the transpose of the back-projection matrix, not a physical line-
@@ -279,6 +298,20 @@ int ifdk_backproject_host(ifdk_plan p, const void *Q_host, int q_dtype, int host
    hence the last bits, may differ between runs). */
 int ifdk_project(ifdk_plan p, const float *vol, float *P, int view_begin, int view_count,
                  void *stream);
+
+/* Output stage of Algorithm 4, I <- reshape(I~) (Sec. 3.3; the volume is
+   stored as Nz slices of Nx x Ny, Sec. 4): writes slices [k_begin,
+   k_begin + k_count) of the k-fastest volume vol (device FP32 [nx][ny][nz],
+   as the back-projectors accumulate it) i-fastest into out (device
+   [k_count][ny][nx] of out_dtype), i.e. out[k - k_begin][j][i] = vol[i][j][k].
+   IFDK_F32 copies exactly; IFDK_F16 / IFDK_BF16 round to nearest even.
+   Both buffers 16-byte aligned, owned by the caller, must not overlap; out
+   is overwritten, vol is only read.  Range errors (k_begin < 0, k_count < 0,
+   k_begin + k_count > nz) return IFDK_ERR_INVALID before any launch;
+   k_count == 0 does nothing (the buffers may then be NULL).  Asynchronous
+   on `stream`. */
+int ifdk_volume_slices(ifdk_plan p, const float *vol, void *out, int out_dtype, int k_begin,
+                       int k_count, void *stream);
 
 /* Reads and clears the plan's device status word on `stream` (synchronises
    that stream).  Returns IFDK_OK, IFDK_ERR_TIMEOUT if a bounded wait inside a

@@ -14,6 +14,7 @@ follows (Chen et al., SC'19, arXiv 1909.02724):
 * ``cosine_weight``, ``ramlak``, ``filter_rows`` -- Algorithm 1
 * ``backproject``, ``backproject_voxels`` -- Algorithm 2 with Algorithm 3
 * ``project`` -- the exact adjoint of ``backproject``
+* ``volume_slices`` -- the output stage of Algorithm 4 (I <- reshape(I~)), in numpy
 
 Geometry is passed as any object with the attributes of
 ``paper_1909_02724_gb300.geometry.Geometry`` (read by attribute name only).
@@ -250,3 +251,37 @@ def project(geom, vol: np.ndarray, view_begin: int = 0, view_count: int | None =
 def fdk(geom, E: np.ndarray, threads: int | None = None) -> np.ndarray:
     """Full FDK in FP64: Algorithm 1 then Algorithm 2."""
     return backproject(geom, filter_views(geom, np.asarray(E, dtype=np.float64)), threads=threads)
+
+
+def round_bf16_bits(x: np.ndarray) -> np.ndarray:
+    """bfloat16 bit patterns (uint16) of FP32 values, rounded to nearest, ties to
+    even: the 32-bit pattern keeps its top 16 bits, plus one when the dropped low
+    16 bits exceed half a unit, or equal it and the kept part is odd (finite
+    values only)."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    hi, lo = b >> 16, b & 0xFFFF
+    up = (lo > 0x8000) | ((lo == 0x8000) & ((hi & 1) == 1))
+    return (hi + up).astype(np.uint16)
+
+
+def volume_slices(vol: np.ndarray, k_begin: int = 0, k_count: int | None = None,
+                  dtype: str = "f32") -> np.ndarray:
+    """Output stage of Algorithm 4, I <- reshape(I~): slices [k_begin, k_begin + k_count)
+    of the k-fastest volume [nx][ny][nz] as an i-fastest [k_count][ny][nx] array,
+    out[k - k_begin][j][i] = vol[i][j][k].  dtype "f32" keeps the FP32 values, "f16"
+    rounds to nearest even (numpy float16), "bf16" returns round_bf16_bits."""
+    vol = np.asarray(vol, dtype=np.float32)
+    nz = vol.shape[2]
+    if k_count is None:
+        k_count = nz - k_begin
+    if k_begin < 0 or k_count < 0 or k_begin + k_count > nz:
+        raise ValueError("slice range outside the volume")
+    out = np.ascontiguousarray(np.transpose(vol[:, :, k_begin:k_begin + k_count], (2, 1, 0)))
+    if dtype == "f32":
+        return out
+    if dtype == "f16":
+        with np.errstate(over="ignore"):      # beyond the largest half: infinity, as rounding gives
+            return out.astype(np.float16)
+    if dtype == "bf16":
+        return round_bf16_bits(out)
+    raise ValueError(dtype)

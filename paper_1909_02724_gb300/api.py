@@ -104,3 +104,42 @@ def fdk_host_pipeline(plan: Plan, E_host: torch.Tensor, vol_host: torch.Tensor, 
     s_out.synchronize()
     s_c.synchronize()
     return vol_host
+
+
+def volume_slices_host(plan: Plan, vol: torch.Tensor, out_host: torch.Tensor, chunk_slices: int = 64,
+                       staging: list | None = None) -> torch.Tensor:
+    """The output stage to host memory: out_host[k][j][i] = vol[i][j][k] for every slice,
+    in out_host's dtype (float32, float16 or bfloat16; pinned for the copies to overlap).
+
+    Slices go in chunks of chunk_slices: ifdk_volume_slices writes chunk c into one of
+    two device staging buffers on the current stream while a copy stream moves chunk
+    c - 1 to the host, so the transpose of one chunk overlaps the copy of the last.
+    staging (optional): two device buffers of at least chunk_slices * ny * nx elements."""
+    g = plan.geom
+    if tuple(out_host.shape) != (g.nz, g.ny, g.nx) or out_host.is_cuda or not out_host.is_contiguous():
+        raise ValueError(f"out_host must be a contiguous host tensor of shape {(g.nz, g.ny, g.nx)}")
+    if chunk_slices < 1:
+        raise ValueError("chunk_slices must be positive")
+    n = min(chunk_slices, g.nz)
+    if staging is None:
+        staging = [torch.empty(n * g.ny * g.nx, dtype=out_host.dtype, device=vol.device) for _ in range(2)]
+    if len(staging) != 2 or any(s.numel() < n * g.ny * g.nx or s.dtype != out_host.dtype for s in staging):
+        raise ValueError("staging must be two device buffers of out_host's dtype, chunk_slices slices each")
+    compute = torch.cuda.current_stream(vol.device)
+    copy = torch.cuda.Stream(vol.device)
+    written = [torch.cuda.Event(), torch.cuda.Event()]
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    for c, k0 in enumerate(range(0, g.nz, n)):
+        kc = min(n, g.nz - k0)
+        b = c % 2
+        buf = staging[b][:kc * g.ny * g.nx].view(kc, g.ny, g.nx)
+        if c >= 2:
+            compute.wait_event(copied[b])          # the copy out of this buffer is done
+        plan.slices(vol, buf, k_begin=k0, k_count=kc, stream=compute)
+        written[b].record(compute)
+        copy.wait_event(written[b])
+        with torch.cuda.stream(copy):
+            out_host[k0:k0 + kc].copy_(buf, non_blocking=True)
+        copied[b].record(copy)
+    copy.synchronize()
+    return out_host

@@ -31,7 +31,8 @@ EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_
            "ifdk_project", "ifdk_last_device_status", "ifdk_set_wait_limit", "ifdk_wait_selftest",
            "ifdk_backproject_info", "ifdk_query_backproject", "ifdk_query_rows", "ifdk_status_string",
            "ifdk_packed_size", "ifdk_pack_views", "ifdk_backproject_packed", "ifdk_set_view_pairing",
-           "ifdk_backproject_packed_info", "ifdk_query_packed")
+           "ifdk_backproject_packed_info", "ifdk_query_packed", "ifdk_volume_slices",
+           "ifdk_set_view_split", "ifdk_view_split")
 
 
 class IfdkError(RuntimeError):
@@ -94,6 +95,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.ifdk_set_view_pairing.argtypes = [vp, i32]
         lib.ifdk_backproject_packed_info.argtypes = [vp, i32, ctypes.POINTER(i64)]
         lib.ifdk_query_packed.argtypes = [ctypes.POINTER(_GeometryC), i32, i32, ctypes.POINTER(i64)]
+        lib.ifdk_volume_slices.argtypes = [vp, vp, vp, i32, i32, i32, vp]
+        lib.ifdk_set_view_split.argtypes = [vp, i32]
+        lib.ifdk_view_split.argtypes = [vp, i32, ctypes.POINTER(i32)]
         lib.ifdk_status_string.argtypes = [i32]
         lib.ifdk_status_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -261,6 +265,21 @@ def ifdk_query_packed(geom: Geometry, q_dtype: int, view_pairing: bool = True) -
 def ifdk_project(plan: int, vol, P, view_begin: int, view_count: int, stream=None) -> None:
     _check(load_library().ifdk_project(plan, _addr(vol), _addr(P), int(view_begin), int(view_count),
                                        _stream(stream)), "ifdk_project")
+
+
+def ifdk_volume_slices(plan: int, vol, out, out_dtype: int, k_begin: int, k_count: int, stream=None) -> None:
+    _check(load_library().ifdk_volume_slices(plan, _addr(vol), _addr(out), int(out_dtype), int(k_begin),
+                                             int(k_count), _stream(stream)), "ifdk_volume_slices")
+
+
+def ifdk_set_view_split(plan: int, max_splits: int) -> None:
+    _check(load_library().ifdk_set_view_split(plan, int(max_splits)), "ifdk_set_view_split")
+
+
+def ifdk_view_split(plan: int, q_dtype: int) -> int:
+    out = ctypes.c_int(0)
+    _check(load_library().ifdk_view_split(plan, int(q_dtype), ctypes.byref(out)), "ifdk_view_split")
+    return int(out.value)
 
 
 def ifdk_last_device_status(plan: int, stream=None) -> int:
@@ -476,6 +495,28 @@ class Plan:
         n = g.np - view_begin if view_count is None else view_count
         ifdk_project(self.handle, vol, P, view_begin, n, stream)
         return P
+
+    def slices(self, vol, out=None, dtype=None, k_begin: int = 0, k_count: int | None = None, stream=None):
+        """Slices [k_begin, k_begin + k_count) of the k-fastest volume, i-fastest:
+        out[k - k_begin][j][i] = vol[i][j][k] (ifdk_volume_slices)."""
+        import torch
+        self._check_vol(vol)
+        g = self.geom
+        n = g.nz - k_begin if k_count is None else k_count
+        if out is None:
+            out = torch.empty((n, g.ny, g.nx), dtype=dtype or torch.float32, device=vol.device)
+        if not out.is_cuda or not out.is_contiguous() or tuple(out.shape) != (n, g.ny, g.nx):
+            raise ValueError(f"out must be a contiguous CUDA tensor of shape ({n}, {g.ny}, {g.nx})")
+        ifdk_volume_slices(self.handle, vol, out, dtype_code(out.dtype), k_begin, n, stream)
+        return out
+
+    def set_view_split(self, max_splits: int) -> None:
+        """Cap on the view split of the packed back-projection (0 automatic, 1 off)."""
+        ifdk_set_view_split(self.handle, max_splits)
+
+    def view_split(self, dtype) -> int:
+        """Parts of the view range a packed back-projection of all views uses (1: none)."""
+        return ifdk_view_split(self.handle, dtype_code(dtype))
 
     def device_status(self, stream=None) -> int:
         return ifdk_last_device_status(self.handle, stream)

@@ -80,6 +80,11 @@ struct PkArgs {
     float cx, cy, cz, uc, vc;
     float wscale, wunscale;             // power of two on the FDK weights (FP16: keeps W in range) and its inverse
     uint32_t stage_bytes, box_tx_bytes;
+    // view split (small volumes): block z takes part z of the view range and writes
+    // (not adds) its sums to part + z * part_stride; nullptr: one part, added to vol
+    float *part;
+    size_t part_stride;
+    int splits;
 };
 
 template <typename T> struct PkT;
@@ -299,22 +304,23 @@ __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], cons
     }
 }
 
-// Writes a z-run: acc[p].x -> voxel k0+p, acc[p].y -> its mirror nz-1-k0-p, of column (i, j).
-template <int L>
-__device__ __forceinline__ void write_run(const PkArgs &a, int k0, int i, int j, const float2 *acc)
+// Writes a z-run: acc[p].x -> voxel k0+p, acc[p].y -> its mirror nz-1-k0-p, of column (i, j)
+// of the volume at dst: added (ADD), or stored (a partial volume of a view split).
+template <int L, bool ADD>
+__device__ __forceinline__ void write_run(const PkArgs &a, float *dst, int k0, int i, int j, const float2 *acc)
 {
     static_assert(L % 4 == 0, "the vector path stores float4 runs from k0 = a multiple of L");
-    float *col = a.vol + ((size_t)i * a.ny + j) * (size_t)a.nz;
+    float *col = dst + ((size_t)i * a.ny + j) * (size_t)a.nz;
     const int half = a.nz / 2, npairs = (a.nz + 1) / 2;
     if ((a.nz & 3) == 0 && k0 + L <= half) {
         float4 *pd = reinterpret_cast<float4 *>(col + k0);
         float4 *pm = reinterpret_cast<float4 *>(col + (a.nz - k0 - L));
 #pragma unroll
         for (int q = 0; q < L / 4; ++q) {
-            float4 d = pd[q];
+            float4 d = ADD ? pd[q] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             d.x += acc[4 * q].x; d.y += acc[4 * q + 1].x; d.z += acc[4 * q + 2].x; d.w += acc[4 * q + 3].x;
             pd[q] = d;
-            float4 m = pm[q];   // voxels nz-k0-L+4q .. +3 mirror pairs L-1-4q .. L-4-4q
+            float4 m = ADD ? pm[q] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // voxels nz-k0-L+4q .. +3: mirror pairs L-1-4q .. L-4-4q
             m.x += acc[L - 1 - 4 * q].y; m.y += acc[L - 2 - 4 * q].y;
             m.z += acc[L - 3 - 4 * q].y; m.w += acc[L - 4 - 4 * q].y;
             pm[q] = m;
@@ -324,9 +330,9 @@ __device__ __forceinline__ void write_run(const PkArgs &a, int k0, int i, int j,
         for (int p = 0; p < L; ++p) {
             const int k = k0 + p;
             if (k < npairs) {
-                col[k] += acc[p].x;
+                col[k] = ADD ? col[k] + acc[p].x : acc[p].x;
                 const int km = a.nz - 1 - k;
-                if (km > k) col[km] += acc[p].y;
+                if (km > k) col[km] = ADD ? col[km] + acc[p].y : acc[p].y;
             }
         }
     }
@@ -375,13 +381,16 @@ __global__ void __launch_bounds__(kThreads, pk_blocks(NV))
     __syncthreads();
     if (lds_u32_v(s0 + kPkAbort) != 0) return;
 
-    const int ngroups = NV * a.view_count;
+    // this block's part of the view range (the whole range without a view split)
+    const int vbeg = a.view_begin + (int)(((long long)a.view_count * blockIdx.z) / a.splits);
+    const int vend = a.view_begin + (int)(((long long)a.view_count * (blockIdx.z + 1)) / a.splits);
+    const int ngroups = NV * (vend - vbeg);
     // Lane 0 of warp 0: window of group t (own view's footprint of the tile),
     // its terms and the TMA box into stage t % S.
     auto issue = [&](int t) {
         const int st = t % S;
         const uint32_t sg = s0 + kPkStage0 + (uint32_t)st * a.stage_bytes;
-        const int s = a.view_begin + (NV == 2 ? (t >> 1) : t);    // view 0 of the box
+        const int s = vbeg + (NV == 2 ? (t >> 1) : t);    // view 0 of the box
         const int own = s + (NV == 2 ? (t & 1) * a.pair_view_off : 0);
         const float4 *tp = reinterpret_cast<const float4 *>(a.terms + own);
         const float4 t0 = __ldg(tp), t1 = __ldg(tp + 1);
@@ -474,6 +483,8 @@ __global__ void __launch_bounds__(kThreads, pk_blocks(NV))
         float2(&c1)[L] = SWAP ? acc[0] : acc[NV - 1];
         // sig < 1 - 2^-10 keeps fp32 rounding of v_{p+1} - v_p below one row; the
         // plan keeps every sig below 1.9 (two rows at most)
+        // (FP32 taps keep the reuse across two-row steps; 16-bit taps load both rows,
+        // which measured faster for them)
         constexpr Reuse WIDE = sizeof(T) == 4 ? Reuse::STEP2 : Reuse::ANY;
         if (__all_sync(0xffffffffu, sig < 0.9990234375f))
             pair_loop<T, NV, L, ROWB, HB, Reuse::STEP1>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1);
@@ -510,8 +521,14 @@ __global__ void __launch_bounds__(kThreads, pk_blocks(NV))
             for (int p = 0; p < L; ++p) acc[n][p] = make_float2(acc[n][p].x * a.wunscale, acc[n][p].y * a.wunscale);
     }
     if (ci < a.nx && cj < a.ny_cols) {
-        write_run<L>(a, k0, ci, cj, acc[0]);
-        if constexpr (NV == 2) write_run<L>(a, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
+        if (a.part == nullptr) {
+            write_run<L, true>(a, a.vol, k0, ci, cj, acc[0]);
+            if constexpr (NV == 2) write_run<L, true>(a, a.vol, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
+        } else {
+            float *dst = a.part + blockIdx.z * a.part_stride;
+            write_run<L, false>(a, dst, k0, ci, cj, acc[0]);
+            if constexpr (NV == 2) write_run<L, false>(a, dst, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
+        }
     }
 }
 
@@ -551,6 +568,42 @@ __global__ void __launch_bounds__(256) pack_kernel(const T *__restrict__ Q, T *_
             *reinterpret_cast<uint2 *>(d) = make_uint2(bits16(v0) | (bits16(v1) << 16), bits16(v2) | (bits16(v3) << 16));
         }
     }
+}
+
+// View split: vol += part[0] + part[1] + ... + part[S-1], element by element in
+// part order (the same order every call, so the result is reproducible).
+__global__ void __launch_bounds__(256) split_reduce_kernel(float *vol, const float *part, size_t n, size_t stride,
+                                                           int S)
+{
+    const size_t step = (size_t)gridDim.x * blockDim.x, n4 = n / 4;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (size_t i = t0; i < n4; i += step) {
+        float4 v = reinterpret_cast<float4 *>(vol)[i];
+        for (int c = 0; c < S; ++c) {
+            const float4 q = __ldcs(reinterpret_cast<const float4 *>(part + c * stride) + i);
+            v.x += q.x; v.y += q.y; v.z += q.z; v.w += q.w;
+        }
+        reinterpret_cast<float4 *>(vol)[i] = v;
+    }
+    for (size_t i = 4 * n4 + t0; i < n; i += step) {
+        float v = vol[i];
+        for (int c = 0; c < S; ++c) v += part[c * stride + i];
+        vol[i] = v;
+    }
+}
+
+// Parts of the view range per launch: enough to fill one wave of the GPU when
+// the grid alone covers at most half of it, each part at least kPkSplitMinUnits
+// pairs (or views), at most the partial volumes the plan holds.
+int pk_splits(const ifdk_plan_s *p, const PkLaunch &b, int units)
+{
+    if (!p->d_split || p->view_split_max == 1) return 1;
+    const long long blocks = (long long)b.grid_x * b.grid_y, want = (long long)p->n_sm * pk_blocks(b.nv);
+    if (blocks * 2 > want) return 1;
+    long long S = std::min<long long>((want + blocks - 1) / blocks, p->split_cap);
+    if (p->view_split_max >= 2) S = std::min<long long>(S, p->view_split_max);
+    S = std::min<long long>(S, units / kPkSplitMinUnits);
+    return S >= 2 ? (int)S : 1;
 }
 
 // Host sizing of the packed kernel: windows from analytic FP64 bounds of the
@@ -653,11 +706,22 @@ int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_beg
     a.wunscale = 1.0f / a.wscale;
     a.stage_bytes = (uint32_t)b.stage_bytes;
     a.box_tx_bytes = (uint32_t)((size_t)b.box_h * NV * BW * 4 * es);
+    const int S = pk_splits(p, b, s_count);
+    a.part = S > 1 ? p->d_split : nullptr;
+    a.part_stride = p->split_stride;
+    a.splits = S;
     void (*kern)(const PkArgs, const CUtensorMap) = bp_packed_kernel<T, NV, BW, pk_pairs(NV, PkT<T>::CODE)>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem) != cudaSuccess)
         return IFDK_ERR_CUDA;
-    kern<<<dim3(b.grid_x, b.grid_y), kThreads, b.smem, stream>>>(a, tmap);
-    return cudaGetLastError() == cudaSuccess ? IFDK_OK : IFDK_ERR_CUDA;
+    kern<<<dim3(b.grid_x, b.grid_y, S), kThreads, b.smem, stream>>>(a, tmap);
+    if (cudaGetLastError() != cudaSuccess) return IFDK_ERR_CUDA;
+    if (S > 1) {
+        const size_t n = (size_t)g.nx * g.ny * g.nz;
+        const size_t blocks = std::min<size_t>((n / 4 + 255) / 256 + 1, (size_t)p->n_sm * 8);
+        split_reduce_kernel<<<(unsigned)blocks, 256, 0, stream>>>(vol, p->d_split, n, p->split_stride, S);
+        if (cudaGetLastError() != cudaSuccess) return IFDK_ERR_CUDA;
+    }
+    return IFDK_OK;
 }
 
 template <typename T, int NV>
@@ -688,6 +752,34 @@ int launch_packed(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin, int 
 }
 
 }  // namespace
+
+int plan_view_split(ifdk_plan_s *p)
+{
+    const ifdk_geometry &g = p->g;
+    if (cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+        return IFDK_ERR_CUDA;
+    const size_t nvox = (size_t)g.nx * g.ny * g.nz;
+    p->split_stride = (nvox + 3) / 4 * 4;   // keeps every partial volume 16-byte aligned
+    bool small = false;
+    for (int d = 0; d < 3; ++d)
+        for (const PkLaunch *b : {&p->pk[d], &p->pk2[d]})
+            if (b->path && (long long)b->grid_x * b->grid_y * 2 <= (long long)p->n_sm * pk_blocks(b->nv)) small = true;
+    if (!small) return IFDK_OK;
+    const size_t cap = std::min<size_t>(kPkMaxSplits, kPkSplitBytes / (p->split_stride * sizeof(float)));
+    if (cap < 2) return IFDK_OK;
+    if (cudaMalloc(&p->d_split, cap * p->split_stride * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return IFDK_ERR_NOMEM;
+    }
+    p->split_cap = (int)cap;
+    return IFDK_OK;
+}
+
+int packed_view_split(const ifdk_plan_s *p, int q_dtype, int units, bool pairs)
+{
+    const PkLaunch &b = pairs ? p->pk2[q_dtype] : p->pk[q_dtype];
+    return b.path ? pk_splits(p, b, units) : 1;
+}
 
 void split_half_turn(int np, int b, int e, int *m)
 {

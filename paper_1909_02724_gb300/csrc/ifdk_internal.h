@@ -54,6 +54,10 @@ constexpr int kPkBoxS = 32, kPkBoxL = 48;   // box widths (elements) the kernel 
 constexpr int pk_pairs(int nv, int q_dtype) { return nv == 2 && q_dtype != IFDK_F16 ? 12 : 16; }
 // resident blocks per SM the packed kernel is built for (registers) and sized for (shared memory)
 constexpr int pk_blocks(int nv) { return nv == 2 ? 2 : 3; }
+// view split of the packed back-projection (small volumes): at most 16 partial
+// volumes of at most 64 MiB together, each part at least 2 pairs (or views)
+constexpr int kPkMaxSplits = 16, kPkSplitMinUnits = 2;
+constexpr size_t kPkSplitBytes = (size_t)64 << 20;
 
 struct PkLaunch {
     int path;          // 1 = packed mirror-pair kernel applies, 0 = not
@@ -100,6 +104,11 @@ struct ifdk_plan_s {
     ifdk::PkLaunch pk[3], pk2[3];        // per storage type: single views / half-turn view pairs
     bool half_turn = false;              // view s + np/2 is view s turned by pi (exactly)
     bool use_half_turn = true;           // caller switch (ifdk_set_view_pairing)
+    // view split: partial volumes [split_cap][split_stride] (allocated only for
+    // small volumes), the caller's cap (0: automatic, 1: off) and the SM count
+    float *d_split = nullptr;
+    size_t split_stride = 0;
+    int split_cap = 0, view_split_max = 0, n_sm = 0;
     unsigned long long wait_ns = 2000000000ull;
     // tensor-core filter: Toeplitz matrix as 3 BF16 planes [3][tc_npad][tc_kpad]
     int tc_kpad = 0, tc_npad = 0;
@@ -125,6 +134,8 @@ int launch_filter_tc(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int t
 int launch_project(ifdk_plan_s *p, const float *vol, float *P, int view_begin, int view_count,
                    cudaStream_t stream);
 int launch_wait_selftest(ifdk_plan_s *p, unsigned long long ns, cudaStream_t stream);
+int launch_volume_slices(ifdk_plan_s *p, const float *vol, void *out, int out_dtype, int k_begin, int k_count,
+                         cudaStream_t stream);
 // Packed views (ifdk_bp_packed.cu).
 void plan_packed(ifdk_plan_s *p);
 size_t packed_view_bytes(const ifdk_plan_s *p, int q_dtype);
@@ -142,6 +153,11 @@ int launch_packed_pairs(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin
 // The views of [b, e) that pair up: s in [b, *m) with partners in [b + np/2, *m + np/2);
 // the rest are [*m, b + np/2) and [*m + np/2, e).  *m = b when nothing pairs.
 void split_half_turn(int np, int b, int e, int *m);
+// View split of the packed back-projection: allocates the partial volumes at
+// plan creation (small volumes only); the parts a launch over `units` pairs
+// (pairs) or views uses.
+int plan_view_split(ifdk_plan_s *p);
+int packed_view_split(const ifdk_plan_s *p, int q_dtype, int units, bool pairs);
 int check_backproject_args(const ifdk_plan_s *p, const void *Q, int q_dtype, int view_begin, int view_count,
                            const float *vol);
 }  // namespace ifdk

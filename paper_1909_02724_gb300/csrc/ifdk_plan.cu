@@ -210,6 +210,8 @@ int ifdk_create(ifdk_plan *out, const ifdk_geometry *gin)
     if (!ok) { cudaGetLastError(); ifdk_destroy(p); return IFDK_ERR_CUDA; }
     plan_backproject(p);
     plan_packed(p);
+    rc = plan_view_split(p);
+    if (rc != IFDK_OK) { ifdk_destroy(p); return rc; }
     *out = p;
     return IFDK_OK;
 }
@@ -230,6 +232,7 @@ int ifdk_destroy(ifdk_plan p)
     cudaFree(p->d_gsum);
     cudaFree(p->d_status);
     cudaFree(p->d_tsplit);
+    cudaFree(p->d_split);
     if (dev >= 0 && dev != p->device) cudaSetDevice(dev);
     delete p;
     return IFDK_OK;
@@ -325,6 +328,22 @@ int ifdk_set_view_pairing(ifdk_plan p, int enable)
     return IFDK_OK;
 }
 
+int ifdk_set_view_split(ifdk_plan p, int max_splits)
+{
+    if (!p || max_splits < 0) return IFDK_ERR_INVALID;
+    p->view_split_max = max_splits;
+    return IFDK_OK;
+}
+
+int ifdk_view_split(ifdk_plan p, int q_dtype, int *splits)
+{
+    if (!p || !splits) return IFDK_ERR_INVALID;
+    if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
+    const bool pairs = p->use_half_turn && p->pk2[q_dtype].path;
+    *splits = packed_view_split(p, q_dtype, pairs ? p->g.np / 2 : p->g.np, pairs);
+    return IFDK_OK;
+}
+
 int ifdk_project(ifdk_plan p, const float *vol, float *P, int view_begin, int view_count, void *stream)
 {
     if (!p || !vol || !P) return IFDK_ERR_INVALID;
@@ -333,6 +352,18 @@ int ifdk_project(ifdk_plan p, const float *vol, float *P, int view_begin, int vi
     if (((uintptr_t)vol & 15) || ((uintptr_t)P & 15)) return IFDK_ERR_ALIGNMENT;
     if (view_count == 0) return IFDK_OK;
     return launch_project(p, vol, P, view_begin, view_count, (cudaStream_t)stream);
+}
+
+int ifdk_volume_slices(ifdk_plan p, const float *vol, void *out, int out_dtype, int k_begin, int k_count,
+                       void *stream)
+{
+    if (!p) return IFDK_ERR_INVALID;
+    if (out_dtype != IFDK_F32 && out_dtype != IFDK_F16 && out_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
+    if (k_begin < 0 || k_count < 0 || k_begin > p->g.nz || k_count > p->g.nz - k_begin) return IFDK_ERR_INVALID;
+    if (k_count == 0) return IFDK_OK;
+    if (!vol || !out) return IFDK_ERR_INVALID;
+    if (((uintptr_t)vol & 15) || ((uintptr_t)out & 15)) return IFDK_ERR_ALIGNMENT;
+    return launch_volume_slices(p, vol, out, out_dtype, k_begin, k_count, (cudaStream_t)stream);
 }
 
 int ifdk_last_device_status(ifdk_plan p, void *stream)

@@ -231,3 +231,48 @@ def test_fdk_host_pipeline_matches_device_fdk():
         fdk_host_pipeline(p, E_host, vol_host, E2, Q, vol2, Qp_dev=Qp, n_steps=n)
         assert torch.equal(vol_host, ref.cpu())
     assert p.device_status() == 0
+
+
+@pytest.mark.parametrize("name", ["fdk64", "ragged", "odd_nz_odd_ny", "magnified_odd_np"])
+@pytest.mark.parametrize("dtype", ["float32", "float16"])
+def test_view_split_small_volumes(name, dtype):
+    """Small volumes split the view range over grid layers (partial volumes summed
+    in part order): reproducible, accumulating, equal to the unsplit launch up to
+    the grouping of the FP32 sums, and within the oracle tolerances."""
+    g = GEOMS[name]
+    p = B.Plan(g)
+    E = phantom_E(g)
+    Q = p.filter(torch.from_numpy(E).cuda(), dtype=TDT[dtype])
+    Qp = p.pack(Q)
+    S = p.view_split(TDT[dtype])
+    assert S >= 2, S                      # these grids cover less than half a wave
+    vol = p.backproject_packed(Qp)
+    assert torch.equal(vol, p.backproject_packed(Qp))
+    ones = torch.ones_like(vol)
+    p.backproject_packed(Qp, ones)
+    assert max_rel((ones - 1).cpu().numpy(), vol.cpu().numpy()) <= 1e-6
+    # a view range that is neither the whole scan nor whole pairs
+    part = p.backproject_packed(Qp, view_begin=1, view_count=g.np - 3)
+    p.set_view_split(3)
+    assert 2 <= p.view_split(TDT[dtype]) <= 3
+    p.set_view_split(1)
+    assert p.view_split(TDT[dtype]) == 1
+    whole = p.backproject_packed(Qp).cpu().numpy()
+    whole_part = p.backproject_packed(Qp, view_begin=1, view_count=g.np - 3).cpu().numpy()
+    v = vol.cpu().numpy()
+    assert max_rel(v, whole) <= 2e-6
+    assert max_rel(part.cpu().numpy(), whole_part) <= 2e-6
+    if dtype == "float32":
+        Qh = Q.cpu().double().numpy()
+        assert rel_l2(v, oracle.backproject(g, Qh)) <= 1e-5
+        assert rel_l2(part.cpu().numpy(), oracle.backproject(g, Qh, 1, g.np - 3)) <= 1e-5
+    assert p.device_status() == 0
+
+
+def test_view_split_off_for_volumes_that_fill_the_gpu():
+    g = scaled_geometry(256, 64, 16)
+    p = B.Plan(g)
+    for dt in TDT.values():
+        assert p.view_split(dt) == 1
+    with pytest.raises(B.IfdkError):
+        p.set_view_split(-1)
