@@ -345,7 +345,9 @@ __device__ __forceinline__ void write_run(const PkArgs &a, float *dst, int k0, i
 constexpr uint32_t kPkFull = 0, kPkEmpty = 64, kPkAbort = 128, kPkLast = 160, kPkStage0 = 256, kPkBox = 128;
 static_assert(kPkMaxStages * 8 <= 64 && kPkLast + 4 * kPkMaxStages <= kPkStage0, "shared-memory map");
 
-template <typename T, int NV, int BW, int L>
+// SPLIT: the launch splits its view range over grid layers (a.part != nullptr);
+// a separate instantiation keeps the whole-range kernel free of it.
+template <typename T, int NV, int BW, int L, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, pk_blocks(NV))
     bp_packed_kernel(const PkArgs a, const __grid_constant__ CUtensorMap tmap)
 {
@@ -382,9 +384,12 @@ __global__ void __launch_bounds__(kThreads, pk_blocks(NV))
     if (lds_u32_v(s0 + kPkAbort) != 0) return;
 
     // this block's part of the view range (the whole range without a view split)
-    const int vbeg = a.view_begin + (int)(((long long)a.view_count * blockIdx.z) / a.splits);
-    const int vend = a.view_begin + (int)(((long long)a.view_count * (blockIdx.z + 1)) / a.splits);
-    const int ngroups = NV * (vend - vbeg);
+    int vbeg = a.view_begin, vcnt = a.view_count;
+    if constexpr (SPLIT) {
+        vbeg = a.view_begin + (int)(((long long)a.view_count * blockIdx.z) / a.splits);
+        vcnt = a.view_begin + (int)(((long long)a.view_count * (blockIdx.z + 1)) / a.splits) - vbeg;
+    }
+    const int ngroups = NV * vcnt;
     // Lane 0 of warp 0: window of group t (own view's footprint of the tile),
     // its terms and the TMA box into stage t % S.
     auto issue = [&](int t) {
@@ -521,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, pk_blocks(NV))
             for (int p = 0; p < L; ++p) acc[n][p] = make_float2(acc[n][p].x * a.wunscale, acc[n][p].y * a.wunscale);
     }
     if (ci < a.nx && cj < a.ny_cols) {
-        if (a.part == nullptr) {
+        if constexpr (!SPLIT) {
             write_run<L, true>(a, a.vol, k0, ci, cj, acc[0]);
             if constexpr (NV == 2) write_run<L, true>(a, a.vol, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
         } else {
@@ -710,7 +715,9 @@ int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_beg
     a.part = S > 1 ? p->d_split : nullptr;
     a.part_stride = p->split_stride;
     a.splits = S;
-    void (*kern)(const PkArgs, const CUtensorMap) = bp_packed_kernel<T, NV, BW, pk_pairs(NV, PkT<T>::CODE)>;
+    constexpr int L = pk_pairs(NV, PkT<T>::CODE);
+    void (*kern)(const PkArgs, const CUtensorMap) =
+        S > 1 ? bp_packed_kernel<T, NV, BW, L, true> : bp_packed_kernel<T, NV, BW, L, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem) != cudaSuccess)
         return IFDK_ERR_CUDA;
     kern<<<dim3(b.grid_x, b.grid_y, S), kThreads, b.smem, stream>>>(a, tmap);

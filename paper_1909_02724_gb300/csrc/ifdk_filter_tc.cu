@@ -265,14 +265,33 @@ __global__ void __launch_bounds__(256)
     const float *Erow = E + grow * nu, *fh_row = fcos + (size_t)v * nu, *fl_row = fcos_lo + (size_t)v * nu;
     float p0, c0;
     weighted(Erow, fh_row, fl_row, k0 - 1, nu, p0, c0);
+    // the 8 weighted elements k0 .. k0 + 7: float4 loads where the rows are 16-byte
+    // aligned (nu a multiple of 4) and the group lies on the detector
+    float pw[8], cw[8];
+    if ((nu & 3) == 0 && k0 + 8 <= nu) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 x = __ldcs(reinterpret_cast<const float4 *>(Erow + k0) + h);
+            const float4 fh = __ldg(reinterpret_cast<const float4 *>(fh_row + k0) + h);
+            const float4 fl = __ldg(reinterpret_cast<const float4 *>(fl_row + k0) + h);
+            const float xs[4] = {x.x, x.y, x.z, x.w}, hs[4] = {fh.x, fh.y, fh.z, fh.w}, ls[4] = {fl.x, fl.y, fl.z, fl.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                pw[4 * h + e] = xs[e] * hs[e];
+                cw[4 * h + e] = fmaf(xs[e], ls[e], fmaf(xs[e], hs[e], -pw[4 * h + e]));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) weighted(Erow, fh_row, fl_row, k0 + e, nu, pw[e], cw[e]);
+    }
     uint32_t w[3][4];
 #pragma unroll
     for (int q = 0; q < 8; q += 2) {
         uint16_t h[3][2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            float p1, c1;
-            weighted(Erow, fh_row, fl_row, k0 + q + e, nu, p1, c1);
+            const float p1 = pw[q + e], c1 = cw[q + e];
             const float s = p1 - p0, bb = s - p1;
             const float err = (p1 - (s - bb)) + (-p0 - bb);   // s + err = p1 - p0 exactly
             float rem = s + (err + (c1 - c0));
