@@ -128,7 +128,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                    accum = empty + 8 * kTcMaxStages;
     const uint32_t tslot = accum + 8, abort_flag = tslot + 4;   // abort_flag + 4: accumulators written
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m_tile = blockIdx.x, n_tile = blockIdx.y;
+    // column tiles fastest: the npad / 128 blocks of one row tile run side by side
+    // and share its data planes in L2 (read from DRAM once, not once per column tile)
+    const int n_tile = blockIdx.x, m_tile = blockIdx.y;
     const int units = a.nk;   // one unit = one K block, all planes of both operands
 
     if (tid == 0) {
@@ -383,7 +385,7 @@ int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size
             cap * kpad);
         a.row0 = r0;
         a.nrows = nr;
-        kern<<<dim3((nr + kTcM - 1) / kTcM, npad / kTcN), kTcThreads, smem, stream>>>(tmA, tmB, a);
+        kern<<<dim3(npad / kTcN, (nr + kTcM - 1) / kTcM), kTcThreads, smem, stream>>>(tmA, tmB, a);
         if (cudaGetLastError() != cudaSuccess) return IFDK_ERR_CUDA;
     }
     return IFDK_OK;
