@@ -16,7 +16,7 @@ a step back-projects the 2048 FP16 filtered views, held in pinned host memory
 zeroed slab, copying them to the device in 64-view chunks on a side stream
 while the back-projection runs; the copies are inside the timed region.
 
---impl reference times the FP64 CPU oracle (the reference of this build) on
+--impl reference times the FP64 CPU oracle (the reference arm: there is no reference code, only the paper) on
 the host cores, each step a bounded sample of the same workload.
 """
 from __future__ import annotations
