@@ -110,9 +110,21 @@ int ifdk_destroy(ifdk_plan p);
    ifdk_filter_workspace_size reports, 128-byte aligned, owned by the caller
    and not used by anything else until the call's work has run (larger
    workspaces process more rows per launch).  split_terms = 0: FP32 SIMT
-   kernel of the direct sum, workspace ignored (may be NULL). */
+   kernel of the same sum by parts, workspace ignored (may be NULL). */
 int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms,
                 void *workspace, size_t workspace_bytes, void *stream);
+
+/* ifdk_filter with the range check of 16-bit storage: also writes
+   view_max[s] = max |Q[s][v][n]| over view s, taken on the FP32 values before
+   the rounding to q_dtype.  Each row's maximum is reduced with warp shuffles
+   in the filter's epilogue, then one atomic max per view and warp.  A value
+   above 65504 means that FP16 storage of the view overflowed to infinity.
+   It is NaN if a value of the view is NaN.  view_max: device FP32 [np],
+   4-byte aligned, owned by the caller, overwritten; the call zeroes it on
+   `stream` first.  Other arguments, the workspace and errors as ifdk_filter;
+   view_max NULL returns IFDK_ERR_INVALID. */
+int ifdk_filter_max(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms,
+                    void *workspace, size_t workspace_bytes, float *view_max, void *stream);
 
 /* Workspace of ifdk_filter for split_terms: the minimum (one 128-row tile of
    split operands) and a preferred size (every row in one launch, up to 1 GiB).

@@ -32,7 +32,7 @@ EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_
            "ifdk_backproject_info", "ifdk_query_backproject", "ifdk_query_rows", "ifdk_status_string",
            "ifdk_packed_size", "ifdk_pack_views", "ifdk_backproject_packed", "ifdk_set_view_pairing",
            "ifdk_backproject_packed_info", "ifdk_query_packed", "ifdk_volume_slices",
-           "ifdk_set_view_split", "ifdk_view_split")
+           "ifdk_set_view_split", "ifdk_view_split", "ifdk_filter_max")
 
 
 class IfdkError(RuntimeError):
@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.ifdk_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_GeometryC)]
         lib.ifdk_destroy.argtypes = [vp]
         lib.ifdk_filter.argtypes = [vp, vp, vp, i32, i32, vp, ctypes.c_size_t, vp]
+        lib.ifdk_filter_max.argtypes = [vp, vp, vp, i32, i32, vp, ctypes.c_size_t, vp, vp]
         lib.ifdk_filter_workspace_size.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_size_t),
                                                    ctypes.POINTER(ctypes.c_size_t)]
         lib.ifdk_filter_noalloc.argtypes = [vp, vp, vp, i32, i32, vp]
@@ -169,6 +170,13 @@ def ifdk_filter(plan: int, E, Q, q_dtype: int, split_terms: int, workspace=None,
                 stream=None) -> None:
     _check(load_library().ifdk_filter(plan, _addr(E), _addr(Q), int(q_dtype), int(split_terms), _addr(workspace),
                                       int(workspace_bytes), _stream(stream)), "ifdk_filter")
+
+
+def ifdk_filter_max(plan: int, E, Q, q_dtype: int, split_terms: int, workspace, workspace_bytes: int, view_max,
+                    stream=None) -> None:
+    _check(load_library().ifdk_filter_max(plan, _addr(E), _addr(Q), int(q_dtype), int(split_terms),
+                                          _addr(workspace), int(workspace_bytes), _addr(view_max), _stream(stream)),
+           "ifdk_filter_max")
 
 
 def ifdk_filter_workspace_size(plan: int, split_terms: int) -> tuple[int, int]:
@@ -359,9 +367,11 @@ class Plan:
         off = (-base) % 128
         return base + off, ws.numel() * 2 - off
 
-    def filter(self, E, Q=None, dtype=None, split_terms: int | None = None, stream=None):
+    def filter(self, E, Q=None, dtype=None, split_terms: int | None = None, stream=None, view_max=None):
         """Algorithm 1 on the tensor cores: split_terms defaults to 3 BF16 terms
-        for FP32 output and 2 for FP16 / BF16 output; 0 selects the SIMT kernel."""
+        for FP32 output and 2 for FP16 / BF16 output; 0 selects the SIMT kernel.
+        view_max (optional): float32 CUDA tensor [np] that receives max |Q| per view
+        in FP32 before the cast (ifdk_filter_max, the 16-bit range check)."""
         import torch
         self._check_views(E, "E")
         if E.dtype != torch.float32:
@@ -372,7 +382,13 @@ class Plan:
         if split_terms is None:
             split_terms = 3 if Q.dtype == torch.float32 else 2
         ws, ws_bytes = self.workspace(split_terms, E.device)
-        ifdk_filter(self.handle, E, Q, dtype_code(Q.dtype), split_terms, ws, ws_bytes, stream)
+        if view_max is None:
+            ifdk_filter(self.handle, E, Q, dtype_code(Q.dtype), split_terms, ws, ws_bytes, stream)
+        else:
+            if (not view_max.is_cuda or view_max.dtype != torch.float32 or not view_max.is_contiguous()
+                    or view_max.numel() != self.geom.np):
+                raise ValueError(f"view_max must be a contiguous float32 CUDA tensor of {self.geom.np} elements")
+            ifdk_filter_max(self.handle, E, Q, dtype_code(Q.dtype), split_terms, ws, ws_bytes, view_max, stream)
         return Q
 
     def filter_adjoint(self, G_Q, out=None, stream=None):

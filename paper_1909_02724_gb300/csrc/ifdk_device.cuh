@@ -111,6 +111,25 @@ __device__ __forceinline__ uint32_t floor_frac(float x, float &frac)
 }
 constexpr uint32_t kFloorBias = 0x4B000000u;  // bits of 2^23
 
+// Per-view maximum of |Q| (the FP16 range check of the filter): m holds the
+// bits of a lane's |value| maximum (|x| bits order like |x|, a NaN above
+// infinity), view its view (-1: nothing).  The lanes of a warp hold rows in
+// view order, so each view is a run of consecutive lanes: a segmented
+// inclusive max-scan with warp shuffles leaves each run's maximum in its
+// last lane, which adds it to vmax[view] with one atomicMax.  All 32 lanes
+// must call it.
+__device__ __forceinline__ void view_max_reduce(unsigned int *vmax, int view, uint32_t m, int lane)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t om = __shfl_up_sync(0xffffffffu, m, d);
+        const int ov = __shfl_up_sync(0xffffffffu, view, d);
+        if (lane >= d && ov == view) m = max(m, om);
+    }
+    const int next = __shfl_down_sync(0xffffffffu, view, 1);
+    if (view >= 0 && (lane == 31 || next != view)) atomicMax(vmax + view, m);
+}
+
 // ---------------------------------------------------------------------------
 // tcgen05 (5th-generation tensor core) helpers: TMEM allocation, MMA issue,
 // commit to an mbarrier, TMEM -> register loads.  cta_group::1 throughout.

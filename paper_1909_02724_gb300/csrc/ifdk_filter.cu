@@ -44,7 +44,7 @@ template <typename TQ, bool ADJ>
 __global__ void __launch_bounds__(kFThreads)
     filter_simt_kernel(const float *__restrict__ E, TQ *__restrict__ Q, const float *__restrict__ fcos,
                        const float *__restrict__ fcos_lo, const float *__restrict__ taps, int nu, int nv,
-                       long long rows)
+                       long long rows, unsigned int *view_max, int view0)
 {
     extern __shared__ float sm[];
     const int len = ADJ ? nu : nu + 1;
@@ -83,7 +83,9 @@ __global__ void __launch_bounds__(kFThreads)
     __syncthreads();
 
     const int n0 = n_lo + threadIdx.x * kOutPerThread;
-    if (n0 >= nu) return;
+    // past the row end: nothing to compute, unless the warp's per-view maximum
+    // needs every lane (the loop below then only reads the tap window)
+    if (n0 >= nu && view_max == nullptr) return;
     float acc[kRows][kOutPerThread];
 #pragma unroll
     for (int r = 0; r < kRows; ++r)
@@ -120,10 +122,25 @@ __global__ void __launch_bounds__(kFThreads)
             }
         }
     }
+    if (!ADJ && view_max != nullptr) {
+        // every lane of the warp holds the same kRows rows: per row, the lanes'
+        // maxima (FP32, before the cast) meet by a butterfly of warp shuffles
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const long long row = r0 + r;
+            uint32_t m = 0u;
+#pragma unroll
+            for (int q = 0; q < kOutPerThread; ++q)
+                if (n0 + q < nu && row < rows) m = max(m, __float_as_uint(acc[r][q]) & 0x7fffffffu);
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
+            if ((threadIdx.x & 31) == 0 && row < rows && m != 0u) atomicMax(view_max + view0 + (int)(row / nv), m);
+        }
+    }
 }
 
 template <typename TQ, bool ADJ>
-int launch_simt(ifdk_plan_s *p, const float *E, void *Q, cudaStream_t stream)
+int launch_simt(ifdk_plan_s *p, const float *E, void *Q, cudaStream_t stream, unsigned int *view_max = nullptr)
 {
     const ifdk_geometry &g = p->g;
     const long long rows = (long long)g.np * g.nv;
@@ -143,7 +160,7 @@ int launch_simt(ifdk_plan_s *p, const float *E, void *Q, cudaStream_t stream)
         const long long nr = rows - r0 < chunk ? rows - r0 : chunk;
         kern<<<dim3(gx, (unsigned)((nr + kRows - 1) / kRows)), kFThreads, smem, stream>>>(
             E + r0 * g.nu, static_cast<TQ *>(Q) + r0 * g.nu, p->d_fcos, p->d_fcos_lo, ADJ ? p->d_taps : p->d_gsum,
-            g.nu, g.nv, nr);
+            g.nu, g.nv, nr, view_max, (int)(r0 / g.nv));
         if (cudaGetLastError() != cudaSuccess) return IFDK_ERR_CUDA;
     }
     return IFDK_OK;
@@ -152,16 +169,16 @@ int launch_simt(ifdk_plan_s *p, const float *E, void *Q, cudaStream_t stream)
 }  // namespace
 
 int launch_filter(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int split_terms, bool adjoint,
-                  cudaStream_t stream)
+                  cudaStream_t stream, unsigned int *view_max)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return IFDK_ERR_CUDA;
     (void)split_terms;
     if (adjoint) return launch_simt<float, true>(p, E, Q, stream);
     switch (q_dtype) {
-    case IFDK_F32: return launch_simt<float, false>(p, E, Q, stream);
-    case IFDK_F16: return launch_simt<__half, false>(p, E, Q, stream);
-    default: return launch_simt<__nv_bfloat16, false>(p, E, Q, stream);
+    case IFDK_F32: return launch_simt<float, false>(p, E, Q, stream, view_max);
+    case IFDK_F16: return launch_simt<__half, false>(p, E, Q, stream, view_max);
+    default: return launch_simt<__nv_bfloat16, false>(p, E, Q, stream, view_max);
     }
 }
 

@@ -63,6 +63,8 @@ struct TcArgs {
     int nrows;            // rows in this chunk
     int nu, nk, npairs;   // K blocks of 64, term pairs
     int planes, stages;   // split terms (planes of each operand per stage), ring depth
+    unsigned int *view_max;   // [np] bits of max |Q| per view (nullptr: not taken)
+    int nv;
 };
 
 // Term pairs (data i, tap j): s = 1, 2, 3 use the first 1, 3, 6.
@@ -80,7 +82,9 @@ template <> __device__ __forceinline__ void store_row32<float>(float *dst, const
         for (int q = 0; q < 8; ++q)
             reinterpret_cast<uint4 *>(dst)[q] = make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
     } else {
-        for (int q = 0; q < n; ++q) dst[q] = __uint_as_float(r[q]);
+#pragma unroll
+        for (int q = 0; q < 32; ++q)   // unrolled: r stays in registers
+            if (q < n) dst[q] = __uint_as_float(r[q]);
     }
 }
 template <typename T16>
@@ -100,7 +104,9 @@ __device__ __forceinline__ void store_row32_16(T16 *dst, const uint32_t (&r)[32]
             reinterpret_cast<uint4 *>(dst)[q] = make_uint4(w[0], w[1], w[2], w[3]);
         }
     } else {
-        for (int q = 0; q < n; ++q) dst[q] = Storage<T16>::from_float(__uint_as_float(r[q]));
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+            if (q < n) dst[q] = Storage<T16>::from_float(__uint_as_float(r[q]));
     }
 }
 template <> __device__ __forceinline__ void store_row32<__half>(__half *dst, const uint32_t (&r)[32], int n)
@@ -207,6 +213,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int lrow = m_tile * kTcM + warp * 32 + lane;
     const long long grow = a.row0 + lrow;
     TQ *Q = static_cast<TQ *>(a.Q);
+    const bool row_ok = ok && !aborted && lrow < a.nrows;
+    uint32_t amax = 0u;   // bits of max |Q| over this thread's row of the tile (FP32, before the cast)
 #pragma unroll 1
     for (int cb = 0; cb < kTcN / 32; ++cb) {
         // sum of the accumulators written, in FP32 (round to nearest)
@@ -224,8 +232,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         const int col = n_tile * kTcN + cb * 32;
         const int n = min(32, a.nu - col);
-        if (ok && !aborted && lrow < a.nrows && n > 0) store_row32<TQ>(Q + grow * a.nu + col, r, n);
+        if (row_ok && n > 0) store_row32<TQ>(Q + grow * a.nu + col, r, n);
+        if (a.view_max && row_ok) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (q < n) amax = max(amax, r[q] & 0x7fffffffu);
+        }
     }
+    if (a.view_max) view_max_reduce(a.view_max, row_ok ? (int)(grow / a.nv) : -1, amax, lane);
     if (!ok || aborted) {
         if (tid == 0) atomicOr(a.status, kStatusTimeout);
     }
@@ -309,8 +323,10 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int t = 0; t < 3; ++t) w[t][q / 2] = (uint32_t)h[t][0] | ((uint32_t)h[t][1] << 16);
     }
-    for (int t = 0; t < planes; ++t)
-        *reinterpret_cast<uint4 *>(ws + t * plane + r * kpad + k0) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+#pragma unroll
+    for (int t = 0; t < 3; ++t)   // unrolled: w stays in registers
+        if (t < planes)
+            *reinterpret_cast<uint4 *>(ws + t * plane + r * kpad + k0) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
 }
 
 uint16_t f2bf(float f)
@@ -350,7 +366,8 @@ int encode_bf16_3d(CUtensorMap *m, const void *base, uint64_t kpad, uint64_t row
 int data_planes(int terms) { return terms; }
 
 template <typename TQ>
-int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size_t ws_bytes, cudaStream_t stream)
+int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size_t ws_bytes, unsigned int *view_max,
+              cudaStream_t stream)
 {
     const ifdk_geometry &g = p->g;
     const int kpad = p->tc_kpad, npad = p->tc_npad, planes = data_planes(terms);
@@ -376,6 +393,8 @@ int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size
     a.nk = kpad / kTcK;
     a.npairs = terms == 3 ? 6 : (terms == 2 ? 3 : 1);
     a.planes = planes;
+    a.view_max = view_max;
+    a.nv = g.nv;
     a.stages = tc_stages(planes);
     for (long long r0 = 0; r0 < rows; r0 += cap) {
         const int nr = (int)(rows - r0 < cap ? rows - r0 : cap);
@@ -429,12 +448,12 @@ size_t filter_workspace_min(const ifdk_plan_s *p, int terms)
 }
 
 int launch_filter_tc(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int terms, void *ws, size_t ws_bytes,
-                     cudaStream_t stream)
+                     cudaStream_t stream, unsigned int *view_max)
 {
     switch (q_dtype) {
-    case IFDK_F32: return launch_tc<float>(p, E, Q, terms, ws, ws_bytes, stream);
-    case IFDK_F16: return launch_tc<__half>(p, E, Q, terms, ws, ws_bytes, stream);
-    default: return launch_tc<__nv_bfloat16>(p, E, Q, terms, ws, ws_bytes, stream);
+    case IFDK_F32: return launch_tc<float>(p, E, Q, terms, ws, ws_bytes, view_max, stream);
+    case IFDK_F16: return launch_tc<__half>(p, E, Q, terms, ws, ws_bytes, view_max, stream);
+    default: return launch_tc<__nv_bfloat16>(p, E, Q, terms, ws, ws_bytes, view_max, stream);
     }
 }
 

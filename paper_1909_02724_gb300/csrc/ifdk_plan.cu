@@ -238,18 +238,40 @@ int ifdk_destroy(ifdk_plan p)
     return IFDK_OK;
 }
 
-int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms, void *workspace,
-                size_t workspace_bytes, void *stream)
+namespace {
+// ifdk_filter and ifdk_filter_max; view_max: nullptr, or [np] zeroed on the stream
+int filter_call(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms, void *workspace,
+                size_t workspace_bytes, float *view_max, void *stream)
 {
     if (!p || !E || !Q) return IFDK_ERR_INVALID;
     if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
     if (split_terms < 0 || split_terms > 3) return IFDK_ERR_INVALID;
-    if (split_terms == 0) return launch_filter(p, E, Q, q_dtype, 0, false, (cudaStream_t)stream);
-    if (!workspace || workspace_bytes < filter_workspace_min(p, split_terms)) return IFDK_ERR_INVALID;
-    if (((uintptr_t)workspace & 127) || ((uintptr_t)E & 15) || ((uintptr_t)Q & 15)) return IFDK_ERR_ALIGNMENT;
+    if (split_terms > 0) {
+        if (!workspace || workspace_bytes < filter_workspace_min(p, split_terms)) return IFDK_ERR_INVALID;
+        if (((uintptr_t)workspace & 127) || ((uintptr_t)E & 15) || ((uintptr_t)Q & 15)) return IFDK_ERR_ALIGNMENT;
+    }
+    if ((uintptr_t)view_max & 3) return IFDK_ERR_ALIGNMENT;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return IFDK_ERR_CUDA;
-    return launch_filter_tc(p, E, Q, q_dtype, split_terms, workspace, workspace_bytes, (cudaStream_t)stream);
+    unsigned int *vm = reinterpret_cast<unsigned int *>(view_max);
+    if (vm && cudaMemsetAsync(vm, 0, sizeof(unsigned int) * p->g.np, (cudaStream_t)stream) != cudaSuccess)
+        return IFDK_ERR_CUDA;
+    if (split_terms == 0) return launch_filter(p, E, Q, q_dtype, 0, false, (cudaStream_t)stream, vm);
+    return launch_filter_tc(p, E, Q, q_dtype, split_terms, workspace, workspace_bytes, (cudaStream_t)stream, vm);
+}
+}  // namespace
+
+int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms, void *workspace,
+                size_t workspace_bytes, void *stream)
+{
+    return filter_call(p, E, Q, q_dtype, split_terms, workspace, workspace_bytes, nullptr, stream);
+}
+
+int ifdk_filter_max(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms, void *workspace,
+                    size_t workspace_bytes, float *view_max, void *stream)
+{
+    if (!view_max) return IFDK_ERR_INVALID;
+    return filter_call(p, E, Q, q_dtype, split_terms, workspace, workspace_bytes, view_max, stream);
 }
 
 int ifdk_filter_workspace_size(ifdk_plan p, int split_terms, size_t *min_bytes, size_t *preferred_bytes)
