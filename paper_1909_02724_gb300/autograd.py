@@ -1,9 +1,11 @@
 """Differentiable operators over the C-ABI kernels.
 
-* ``backproject(Q, plan)``: Algorithm 4; its backward is ``ifdk_project``
-  (the exact transpose of the back-projection matrix).
-* ``project(vol, plan)``: the adjoint projector; its backward is
-  ``ifdk_backproject``.
+* ``backproject(Q, plan)``: Algorithm 4 (the packed kernel where the plan
+  has one, else ``ifdk_backproject``; the same operator up to FP32 rounding);
+  its backward is ``ifdk_project`` (the exact transpose of the back-projection
+  matrix).
+* ``project(vol, plan)``: the adjoint projector; its backward is the
+  back-projection above.
 * ``filter(E, plan)``: Algorithm 1 in FP32; its backward is
   ``ifdk_filter_adjoint`` (F_cos . T with T symmetric, because h is even).
 
@@ -26,11 +28,19 @@ def _f32(t: torch.Tensor) -> torch.Tensor:
     return t.contiguous()
 
 
+def _backproject(plan: Plan, Q: torch.Tensor) -> torch.Tensor:
+    """Back-projection of all views: packed views (ifdk_pack_views +
+    ifdk_backproject_packed) where the plan has them, else ifdk_backproject."""
+    if plan.has_packed(torch.float32):
+        return plan.backproject_packed(plan.pack(Q))
+    return plan.backproject(Q)
+
+
 class BackprojectFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, Q, plan: Plan):
         ctx.plan = plan
-        return plan.backproject(_f32(Q))
+        return _backproject(plan, _f32(Q))
 
     @staticmethod
     def backward(ctx, g_vol):
@@ -49,7 +59,7 @@ class ProjectFn(torch.autograd.Function):
     def backward(ctx, g_P):
         if not ctx.needs_input_grad[0]:
             return None, None
-        return ctx.plan.backproject(_f32(g_P)), None
+        return _backproject(ctx.plan, _f32(g_P)), None
 
 
 class FilterFn(torch.autograd.Function):

@@ -95,7 +95,7 @@ def test_fdk_end_to_end(name, dtype):
         assert rel_l2(vol, ref) <= 2e-3, rel_l2(vol, ref)
 
 
-@pytest.mark.parametrize("name", ["fdk64", "ragged", "offsets_general", "tiny8"])
+@pytest.mark.parametrize("name", list(GEOMS))
 def test_project_matches_oracle_adjoint(name):
     g = GEOMS[name]
     rng = np.random.default_rng(1)
