@@ -283,6 +283,23 @@ int ifdk_backproject_host(ifdk_plan p, const void *Q_host, int q_dtype, int host
                           int view_begin, int view_count, int chunk_views, void *staging,
                           size_t staging_bytes, float *vol, void *stream);
 
+/* Short scans (the scan variant beyond the Delta-beta rule).  A scan over
+   pi + 2 delta with delta > the largest fan angle gamma measures some rays
+   twice: (beta, gamma) again as (beta + pi + 2 gamma, -gamma).  enable = 1
+   makes ifdk_filter, ifdk_filter_max, ifdk_filter_noalloc and
+   ifdk_filter_adjoint also weight every projection by 2 w(beta_s, gamma_u)
+   before the ramp filter.  w is Parker's weight (Med. Phys. 9, 1982), and a
+   ray's two weights add to 1; the factor 2 replaces the 1/2 that the
+   full-scan FDK constant holds for the double cover.  beta_s is measured from
+   angles[0] and gamma_u = atan((u - u_c) Du / D).  The weights are formed in
+   FP64 on the host and stored as FP32 [np][nu] in device memory owned by the
+   plan.  The view weights stay those of ifdk_create; the first and last views
+   get w = 0.  Returns IFDK_ERR_GEOMETRY unless the angles increase strictly
+   over a range in (pi + 2 max|gamma|, 2 pi) with np >= 3; IFDK_ERR_NOMEM if
+   the table cannot be allocated.  enable = 0 drops the weights.  Not safe to
+   call while filter calls of the plan are in flight. */
+int ifdk_set_short_scan(ifdk_plan p, int enable);
+
 /* View split of the packed back-projection for small volumes.  Throughput
    falls as the volume shrinks against its input (the alpha of Table 5).
    A small volume has too few columns and z-runs to fill the GPU: its grid

@@ -15,6 +15,9 @@ follows (Chen et al., SC'19, arXiv 1909.02724):
 * ``backproject``, ``backproject_voxels`` -- Algorithm 2 with Algorithm 3
 * ``project`` -- the exact adjoint of ``backproject``
 * ``volume_slices`` -- the output stage of Algorithm 4 (I <- reshape(I~)), in numpy
+* ``parker_weight``, ``short_scan_weights`` -- short-scan redundancy weights
+  (Parker, Med. Phys. 9, 1982; not in the paper), in numpy; ``filter_rows`` /
+  ``filter_views`` apply them for geometries with ``short_scan`` set
 
 Geometry is passed as any object with the attributes of
 ``paper_1909_02724_gb300.geometry.Geometry`` (read by attribute name only).
@@ -149,14 +152,49 @@ def ramlak(n: int) -> np.ndarray:
     return out
 
 
-def filter_rows(geom, E_rows: np.ndarray, rows_v: np.ndarray, method: str = "auto") -> np.ndarray:
+def parker_weight(beta, gamma, delta):
+    """Parker's weight of the ray (beta, gamma) of a scan over [0, pi + 2 delta]:
+    sin^2(pi/4 beta / (delta - gamma)) up to beta = 2 delta - 2 gamma, 1 up to
+    pi - 2 gamma, sin^2(pi/4 (pi + 2 delta - beta) / (delta + gamma)) to the end,
+    0 outside the scan."""
+    b, gm = np.broadcast_arrays(np.asarray(beta, np.float64), np.asarray(gamma, np.float64))
+    w = np.zeros(b.shape)
+    rise = (b >= 0) & (b < 2 * delta - 2 * gm)
+    flat = (b >= 2 * delta - 2 * gm) & (b <= np.pi - 2 * gm)
+    fall = (b > np.pi - 2 * gm) & (b <= np.pi + 2 * delta)
+    w[rise] = np.sin(np.pi / 4 * b[rise] / (delta - gm[rise])) ** 2
+    w[flat] = 1.0
+    w[fall] = np.sin(np.pi / 4 * (np.pi + 2 * delta - b[fall]) / (delta + gm[fall])) ** 2
+    return w
+
+
+def short_scan_weights(geom) -> np.ndarray:
+    """(np, nu) factors 2 w(beta_s - beta_0, gamma_u) of a short scan, gamma_u the fan
+    angle atan((u - u_c) Du / D) of column u and delta = (scan range - pi) / 2.  The 2
+    replaces the 1/2 that the full-scan FDK constant (Kak-Slaney) holds for the rays'
+    double cover."""
+    uc = (geom.nu - 1) / 2.0 + geom.off_u / geom.du
+    gamma = np.arctan((np.arange(geom.nu) - uc) * geom.du / geom.sdd)
+    beta = np.asarray(geom.angles, np.float64) - geom.angles[0]
+    delta = 0.5 * (beta[-1] - np.pi)
+    assert np.all(np.diff(beta) > 0) and delta > np.abs(gamma).max() and beta[-1] < 2 * np.pi
+    return 2.0 * parker_weight(beta[:, None], gamma[None, :], delta)
+
+
+def filter_rows(geom, E_rows: np.ndarray, rows_v: np.ndarray, method: str = "auto",
+                rows_s: np.ndarray | None = None) -> np.ndarray:
     """Algorithm 1 on selected rows: Q = F_ramp (x) (E . F_cos).
 
     E_rows: (R, nu) raw projection rows; rows_v: (R,) detector row index of each
     (selects the F_cos row).  method: 'direct', 'fft' or 'auto' (fft for nu >= 256).
+    rows_s: (R,) view index of each row, needed for a short-scan geometry (its rows
+    are weighted by short_scan_weights before the filter).
     """
     lib, g = _load(), _GeomHolder(geom)
     E_rows = np.ascontiguousarray(E_rows, dtype=np.float64).reshape(-1, geom.nu)
+    if getattr(geom, "short_scan", False):
+        assert rows_s is not None, "short-scan rows need their view indices"
+        E_rows = np.ascontiguousarray(E_rows * short_scan_weights(geom)[np.asarray(rows_s)])
     rows_v = np.ascontiguousarray(rows_v, dtype=np.int32).reshape(-1)
     assert rows_v.shape[0] == E_rows.shape[0]
     Q = np.empty_like(E_rows)
@@ -185,7 +223,8 @@ def filter_views(geom, E: np.ndarray, method: str = "auto") -> np.ndarray:
     """Algorithm 1 on whole views: E (np, nv, nu) -> Q (np, nv, nu)."""
     npv = E.shape[0]
     rows_v = np.tile(np.arange(geom.nv, dtype=np.int32), npv)
-    return filter_rows(geom, E.reshape(-1, geom.nu), rows_v, method).reshape(E.shape)
+    rows_s = np.repeat(np.arange(npv), geom.nv)
+    return filter_rows(geom, E.reshape(-1, geom.nu), rows_v, method, rows_s).reshape(E.shape)
 
 
 def backproject(geom, Q: np.ndarray, view_begin: int = 0, view_count: int | None = None,

@@ -32,7 +32,7 @@ EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_
            "ifdk_backproject_info", "ifdk_query_backproject", "ifdk_query_rows", "ifdk_status_string",
            "ifdk_packed_size", "ifdk_pack_views", "ifdk_backproject_packed", "ifdk_set_view_pairing",
            "ifdk_backproject_packed_info", "ifdk_query_packed", "ifdk_volume_slices",
-           "ifdk_set_view_split", "ifdk_view_split", "ifdk_filter_max")
+           "ifdk_set_view_split", "ifdk_view_split", "ifdk_filter_max", "ifdk_set_short_scan")
 
 
 class IfdkError(RuntimeError):
@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.ifdk_query_packed.argtypes = [ctypes.POINTER(_GeometryC), i32, i32, ctypes.POINTER(i64)]
         lib.ifdk_volume_slices.argtypes = [vp, vp, vp, i32, i32, i32, vp]
         lib.ifdk_set_view_split.argtypes = [vp, i32]
+        lib.ifdk_set_short_scan.argtypes = [vp, i32]
         lib.ifdk_view_split.argtypes = [vp, i32, ctypes.POINTER(i32)]
         lib.ifdk_status_string.argtypes = [i32]
         lib.ifdk_status_string.restype = ctypes.c_char_p
@@ -280,6 +281,10 @@ def ifdk_volume_slices(plan: int, vol, out, out_dtype: int, k_begin: int, k_coun
                                              int(k_count), _stream(stream)), "ifdk_volume_slices")
 
 
+def ifdk_set_short_scan(plan: int, enable: bool) -> None:
+    _check(load_library().ifdk_set_short_scan(plan, 1 if enable else 0), "ifdk_set_short_scan")
+
+
 def ifdk_set_view_split(plan: int, max_splits: int) -> None:
     _check(load_library().ifdk_set_view_split(plan, int(max_splits)), "ifdk_set_view_split")
 
@@ -328,6 +333,12 @@ class Plan:
         self.geom = geom
         self._ws = {}
         self.handle = ifdk_create(geom)
+        if getattr(geom, "short_scan", False):
+            try:
+                ifdk_set_short_scan(self.handle, True)
+            except Exception:
+                self.close()
+                raise
 
     def close(self) -> None:
         if self.handle:

@@ -111,6 +111,15 @@ __device__ __forceinline__ uint32_t floor_frac(float x, float &frac)
 }
 constexpr uint32_t kFloorBias = 0x4B000000u;  // bits of 2^23
 
+// (p + c) * s for a double-float p + c and an FP32 scale s, as a double-float:
+// the product's rounding error is recovered by an FMA (the short-scan weights).
+__device__ __forceinline__ void df_scale(float &p, float &c, float s)
+{
+    const float q = p * s;
+    c = fmaf(c, s, fmaf(p, s, -q));
+    p = q;
+}
+
 // Per-view maximum of |Q| (the FP16 range check of the filter): m holds the
 // bits of a lane's |value| maximum (|x| bits order like |x|, a NaN above
 // infinity), view its view (-1: nothing).  The lanes of a warp hold rows in

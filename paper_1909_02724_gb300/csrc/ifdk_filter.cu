@@ -25,8 +25,10 @@ constexpr int kFThreads = 256;
 constexpr int kOutPerBlock = kFThreads * kOutPerThread;
 
 // Weighted sample w(m) = E F_cos as a double-float p + c; 0 outside [0, nu).
+// srow (short scan, else nullptr): the view's per-column redundancy weights.
 __device__ __forceinline__ void weighted_df(const float *__restrict__ Erow, const float *__restrict__ fh_row,
-                                            const float *__restrict__ fl_row, int m, int nu, float &p, float &c)
+                                            const float *__restrict__ fl_row, const float *__restrict__ srow, int m,
+                                            int nu, float &p, float &c)
 {
     p = 0.0f;
     c = 0.0f;
@@ -34,6 +36,7 @@ __device__ __forceinline__ void weighted_df(const float *__restrict__ Erow, cons
         const float x = __ldg(Erow + m), fh = __ldg(fh_row + m);
         p = x * fh;
         c = fmaf(x, __ldg(fl_row + m), fmaf(x, fh, -p));
+        if (srow) df_scale(p, c, __ldg(srow + m));
     }
 }
 
@@ -44,7 +47,7 @@ template <typename TQ, bool ADJ>
 __global__ void __launch_bounds__(kFThreads)
     filter_simt_kernel(const float *__restrict__ E, TQ *__restrict__ Q, const float *__restrict__ fcos,
                        const float *__restrict__ fcos_lo, const float *__restrict__ taps, int nu, int nv,
-                       long long rows, unsigned int *view_max, int view0)
+                       long long rows, unsigned int *view_max, int view0, const float *__restrict__ sweight)
 {
     extern __shared__ float sm[];
     const int len = ADJ ? nu : nu + 1;
@@ -62,9 +65,10 @@ __global__ void __launch_bounds__(kFThreads)
                     x = __ldg(E + row * nu + m);
                 } else {
                     const size_t vo = (size_t)(row % nv) * nu;
+                    const float *srow = sweight ? sweight + (size_t)(view0 + row / nv) * nu : nullptr;
                     float p1, c1, p0, c0;
-                    weighted_df(E + row * nu, fcos + vo, fcos_lo + vo, m, nu, p1, c1);
-                    weighted_df(E + row * nu, fcos + vo, fcos_lo + vo, m - 1, nu, p0, c0);
+                    weighted_df(E + row * nu, fcos + vo, fcos_lo + vo, srow, m, nu, p1, c1);
+                    weighted_df(E + row * nu, fcos + vo, fcos_lo + vo, srow, m - 1, nu, p0, c0);
                     const float s = p1 - p0, bb = s - p1;
                     const float err = (p1 - (s - bb)) + (-p0 - bb);   // s + err = p1 - p0 exactly
                     x = s + (err + (c1 - c0));
@@ -117,7 +121,10 @@ __global__ void __launch_bounds__(kFThreads)
             const int n = n0 + q;
             if (n < nu) {
                 float y = acc[r][q];
-                if (ADJ) y *= __ldg(fcos + (row % nv) * nu + n);
+                if (ADJ) {
+                    y *= __ldg(fcos + (row % nv) * nu + n);
+                    if (sweight) y *= __ldg(sweight + (size_t)(view0 + row / nv) * nu + n);
+                }
                 Q[row * nu + n] = Storage<TQ>::from_float(y);
             }
         }
@@ -160,7 +167,7 @@ int launch_simt(ifdk_plan_s *p, const float *E, void *Q, cudaStream_t stream, un
         const long long nr = rows - r0 < chunk ? rows - r0 : chunk;
         kern<<<dim3(gx, (unsigned)((nr + kRows - 1) / kRows)), kFThreads, smem, stream>>>(
             E + r0 * g.nu, static_cast<TQ *>(Q) + r0 * g.nu, p->d_fcos, p->d_fcos_lo, ADJ ? p->d_taps : p->d_gsum,
-            g.nu, g.nv, nr, view_max, (int)(r0 / g.nv));
+            g.nu, g.nv, nr, view_max, (int)(r0 / g.nv), p->d_sweight);
         if (cudaGetLastError() != cudaSuccess) return IFDK_ERR_CUDA;
     }
     return IFDK_OK;

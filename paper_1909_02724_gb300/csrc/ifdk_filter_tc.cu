@@ -268,8 +268,8 @@ __device__ __forceinline__ void weighted(const float *__restrict__ Erow, const f
 // once to FP32.
 __global__ void __launch_bounds__(256)
     filter_split_kernel(const float *__restrict__ E, const float *__restrict__ fcos, const float *__restrict__ fcos_lo,
-                        __nv_bfloat16 *ws, int nu, int nv, int kpad, long long row0, int nrows, int planes,
-                        long long plane)
+                        const float *__restrict__ sweight, __nv_bfloat16 *ws, int nu, int nv, int kpad, long long row0,
+                        int nrows, int planes, long long plane)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int groups = kpad / 8;
@@ -300,6 +300,14 @@ __global__ void __launch_bounds__(256)
     } else {
 #pragma unroll
         for (int e = 0; e < 8; ++e) weighted(Erow, fh_row, fl_row, k0 + e, nu, pw[e], cw[e]);
+    }
+    if (sweight) {
+        // short scan: the per-(view, column) redundancy weight, applied with F_cos
+        const float *srow = sweight + (grow / nv) * nu;
+        if (k0 > 0) df_scale(p0, c0, __ldg(srow + k0 - 1));
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (k0 + e < nu) df_scale(pw[e], cw[e], __ldg(srow + k0 + e));
     }
     uint32_t w[3][4];
 #pragma unroll
@@ -400,8 +408,8 @@ int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size
         const int nr = (int)(rows - r0 < cap ? rows - r0 : cap);
         const long long threads = (long long)nr * (kpad / 8);
         filter_split_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(
-            E, p->d_fcos, p->d_fcos_lo, static_cast<__nv_bfloat16 *>(ws), g.nu, g.nv, kpad, r0, nr, planes,
-            cap * kpad);
+            E, p->d_fcos, p->d_fcos_lo, p->d_sweight, static_cast<__nv_bfloat16 *>(ws), g.nu, g.nv, kpad, r0, nr,
+            planes, cap * kpad);
         a.row0 = r0;
         a.nrows = nr;
         kern<<<dim3(npad / kTcN, (nr + kTcM - 1) / kTcM), kTcThreads, smem, stream>>>(tmA, tmB, a);

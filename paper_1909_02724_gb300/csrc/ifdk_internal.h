@@ -104,6 +104,8 @@ struct ifdk_plan_s {
     ifdk::PkLaunch pk[3], pk2[3];        // per storage type: single views / half-turn view pairs
     bool half_turn = false;              // view s + np/2 is view s turned by pi (exactly)
     bool use_half_turn = true;           // caller switch (ifdk_set_view_pairing)
+    // short scan: 2 w(beta_s, gamma_u) per (view, column), [np][nu] (nullptr: full scan)
+    float *d_sweight = nullptr;
     // view split: partial volumes [split_cap][split_stride] (allocated only for
     // small volumes), the caller's cap (0: automatic, 1: off) and the SM count
     float *d_split = nullptr;

@@ -233,6 +233,7 @@ int ifdk_destroy(ifdk_plan p)
     cudaFree(p->d_status);
     cudaFree(p->d_tsplit);
     cudaFree(p->d_split);
+    cudaFree(p->d_sweight);
     if (dev >= 0 && dev != p->device) cudaSetDevice(dev);
     delete p;
     return IFDK_OK;
@@ -347,6 +348,56 @@ int ifdk_set_view_pairing(ifdk_plan p, int enable)
 {
     if (!p || (enable != 0 && enable != 1)) return IFDK_ERR_INVALID;
     p->use_half_turn = enable != 0;
+    return IFDK_OK;
+}
+
+namespace {
+// Parker's redundancy weight of the ray (beta, gamma) of a short scan over
+// [0, pi + 2 delta]: the ray (beta, gamma) is measured again as
+// (beta + pi + 2 gamma, -gamma), and the two weights add to 1.
+double parker_weight(double b, double gm, double d)
+{
+    if (b < 0.0 || b > M_PI + 2.0 * d) return 0.0;
+    if (b < 2.0 * d - 2.0 * gm) {
+        const double t = std::sin(M_PI / 4.0 * b / (d - gm));
+        return t * t;
+    }
+    if (b <= M_PI - 2.0 * gm) return 1.0;
+    const double t = std::sin(M_PI / 4.0 * (M_PI + 2.0 * d - b) / (d + gm));
+    return t * t;
+}
+}  // namespace
+
+int ifdk_set_short_scan(ifdk_plan p, int enable)
+{
+    if (!p || (enable != 0 && enable != 1)) return IFDK_ERR_INVALID;
+    if (!enable) {
+        cudaFree(p->d_sweight);
+        p->d_sweight = nullptr;
+        return IFDK_OK;
+    }
+    const ifdk_geometry &g = p->g;
+    if (g.np < 3) return IFDK_ERR_GEOMETRY;
+    for (int s = 1; s < g.np; ++s)
+        if (!(g.angles[s] > g.angles[s - 1])) return IFDK_ERR_GEOMETRY;
+    std::vector<double> gamma(g.nu);
+    double gmax = 0.0;
+    for (int u = 0; u < g.nu; ++u) {
+        gamma[u] = std::atan((u - p->uc) * g.du / g.sdd);   // fan angle of column u
+        gmax = std::max(gmax, std::fabs(gamma[u]));
+    }
+    const double range = g.angles[g.np - 1] - g.angles[0], delta = 0.5 * (range - M_PI);
+    if (!(delta > gmax) || !(range < 2.0 * M_PI)) return IFDK_ERR_GEOMETRY;
+    std::vector<float> w((size_t)g.np * g.nu);
+    for (int s = 0; s < g.np; ++s)
+        for (int u = 0; u < g.nu; ++u)   // 2 w: the full-scan FDK constant holds a 1/2 for the double cover
+            w[(size_t)s * g.nu + u] = (float)(2.0 * parker_weight(g.angles[s] - g.angles[0], gamma[u], delta));
+    if (!p->d_sweight && cudaMalloc(&p->d_sweight, sizeof(float) * w.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return IFDK_ERR_NOMEM;
+    }
+    if (cudaMemcpy(p->d_sweight, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return IFDK_ERR_CUDA;
     return IFDK_OK;
 }
 

@@ -33,6 +33,7 @@ class Geometry:
     off_v: float = 0.0
     vol_off_z: float = 0.0     # world Z of the volume centre (mm)
     view_weights: np.ndarray | None = field(default=None)  # per-view angular weights (rad)
+    short_scan: bool = False   # Parker redundancy weights (scan over pi + 2 delta)
 
     def __post_init__(self):
         self.angles = np.ascontiguousarray(np.asarray(self.angles, dtype=np.float64).reshape(-1))
@@ -69,6 +70,23 @@ def circular(n_views: int, nu: int, nv: int, du: float, dv: float, nx: int, ny: 
     angles = start + arc * np.arange(n_views, dtype=np.float64) / n_views
     return Geometry(sid=sid, sdd=sdd, nu=nu, nv=nv, du=du, dv=dv, angles=angles, nx=nx, ny=ny,
                     nz=nz, dx=dx, dy=dx if dy is None else dy, dz=dx if dz is None else dz, **kw)
+
+
+def fan_half_angle(nu: int, du: float, sdd: float, off_u: float = 0.0) -> float:
+    """Largest |gamma| = |atan((u - u_c) Du / D)| over the detector columns."""
+    uc = (nu - 1) / 2.0 + off_u / du
+    return float(max(abs(np.arctan(-uc * du / sdd)), abs(np.arctan((nu - 1 - uc) * du / sdd))))
+
+
+def short_scan(n_views: int, nu: int, nv: int, du: float, dv: float, nx: int, ny: int, nz: int,
+               dx: float, overscan: float = 0.02, start: float = 0.0, **kw) -> Geometry:
+    """A short scan: n_views uniform views from start to start + pi + 2 delta (both
+    ends included), delta = the fan half-angle + overscan (rad)."""
+    sdd = kw.get("sdd", 1500.0)
+    delta = fan_half_angle(nu, du, sdd, kw.get("off_u", 0.0)) + overscan
+    arc = np.pi + 2.0 * delta
+    g = circular(n_views, nu, nv, du, dv, nx, ny, nz, dx, arc=arc * n_views / (n_views - 1), start=start, **kw)
+    return g.with_(short_scan=True)
 
 
 def gups(geom_or_updates, seconds: float) -> float:
