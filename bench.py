@@ -313,7 +313,7 @@ def run_ours(args):
         vol_host = torch.empty(vol.shape, dtype=torch.float32, pin_memory=True)
         E2 = [E, torch.empty_like(E)]
         vol2 = [vol, torch.empty_like(vol)]
-        e_steps = max(3, min(args.steps, 10))
+        e_steps = max(3, min(args.steps, 20))
         fdk_host(plan, E_host, vol_host, E, Q, vol, Qp_dev=Qp)                  # one serial step (warm)
         fdk_host_pipeline(plan, E_host, vol_host, E2, Q, vol2, Qp_dev=Qp, n_steps=2)
         if world > 1:
