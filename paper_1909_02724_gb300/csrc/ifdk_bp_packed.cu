@@ -85,6 +85,7 @@ struct PkArgs {
     float *part;
     size_t part_stride;
     int splits;
+    int zfull;                          // z-blocks of L pairs; the rest take kPkTailL pairs
 };
 
 template <typename T> struct PkT;
@@ -347,9 +348,9 @@ static_assert(kPkMaxStages * 8 <= 64 && kPkLast + 4 * kPkMaxStages <= kPkStage0,
 
 // SPLIT: the launch splits its view range over grid layers (a.part != nullptr);
 // a separate instantiation keeps the whole-range kernel free of it.
+// One block's work: the z-run of L pairs from pair k0 of a 16 x 16 column tile.
 template <typename T, int NV, int BW, int L, bool SPLIT>
-__global__ void __launch_bounds__(kThreads, pk_blocks(NV))
-    bp_packed_kernel(const PkArgs a, const __grid_constant__ CUtensorMap tmap)
+__device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tmap, const int k0)
 {
     constexpr uint32_t ES = Tap<T>::ES;
     constexpr int ALIGN = PkT<T>::ALIGN;
@@ -365,7 +366,6 @@ __global__ void __launch_bounds__(kThreads, pk_blocks(NV))
 
     // block coordinates: warp = 16 x 2 patch of columns, 8 warps per 16 x 16 tile
     const int i0 = (blockIdx.x % a.tiles_x) * kTileX, j0 = (blockIdx.x / a.tiles_x) * kTileY;
-    const int k0 = blockIdx.y * L;
     const int ci = i0 + (lane & 15), cj = j0 + warp * 2 + (lane >> 4);
     const float ip = (float)ci - a.cx, jp = (float)cj - a.cy, kp0 = (float)k0 - a.cz;
 
@@ -537,6 +537,23 @@ __global__ void __launch_bounds__(kThreads, pk_blocks(NV))
     }
 }
 
+// z-blocks 0 .. zfull - 1 take L pairs each; the blocks after them take the
+// remaining npairs - zfull L pairs kPkTailL at a time, so that no block runs
+// pairs past the volume's middle.
+template <typename T, int NV, int BW, int L, bool SPLIT>
+__global__ void __launch_bounds__(kThreads, pk_blocks(NV))
+    bp_packed_kernel(const PkArgs a, const __grid_constant__ CUtensorMap tmap)
+{
+    if constexpr (L == kPkTailL) {
+        pk_block<T, NV, BW, L, SPLIT>(a, tmap, (int)blockIdx.y * L);
+    } else {
+        if ((int)blockIdx.y < a.zfull)
+            pk_block<T, NV, BW, L, SPLIT>(a, tmap, (int)blockIdx.y * L);
+        else
+            pk_block<T, NV, BW, kPkTailL, SPLIT>(a, tmap, a.zfull * L + ((int)blockIdx.y - a.zfull) * kPkTailL);
+    }
+}
+
 // Packing: element e of row r of view s, column c = e - 1:
 // (Q[r][c], Q[2vc-r][c], Q[r][c+1] - Q[r][c], Q[2vc-r][c+1] - Q[2vc-r][c]),
 // the differences formed in FP32 and rounded once to T.
@@ -625,7 +642,7 @@ PkLaunch size_packed(const ifdk_plan_s *p, int q_dtype, int nv)
     const int tiles_x = (g.nx + kTileX - 1) / kTileX, tiles_y = (ny_cols + kTileY - 1) / kTileY;
     const int L = pk_pairs(nv, q_dtype), npairs = (g.nz + 1) / 2, zblocks = (npairs + L - 1) / L;
     b.grid_x = tiles_x * tiles_y;
-    b.grid_y = zblocks;
+    b.grid_y = pk_zblocks(npairs, L);
     if (!p->fold_ok) return b;
     if (nv == 2 && (!p->half_turn || g.ny % 2 != 0)) return b;
     const double cx = (g.nx - 1) / 2.0, cy = (g.ny - 1) / 2.0, cz = (g.nz - 1) / 2.0;
@@ -654,7 +671,7 @@ PkLaunch size_packed(const ifdk_plan_s *p, int q_dtype, int nv)
     if (b.stages < 3) b.stages = 3;   // fewer blocks per SM rather than a shallower ring
     b.smem = 128 + kPkStage0 + (size_t)b.stages * b.stage_bytes;
     if (b.smem > 220 * 1024) return b;
-    if ((size_t)g.np * p->pk_rows * p->pk_nu * 4 * es >= ((size_t)1 << 40) || zblocks > 65535) return b;
+    if ((size_t)g.np * p->pk_rows * p->pk_nu * 4 * es >= ((size_t)1 << 40) || b.grid_y > 65535) return b;
     b.pairs = L;
     b.path = 1;
     return b;
@@ -711,6 +728,7 @@ int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_beg
     a.wunscale = 1.0f / a.wscale;
     a.stage_bytes = (uint32_t)b.stage_bytes;
     a.box_tx_bytes = (uint32_t)((size_t)b.box_h * NV * BW * 4 * es);
+    a.zfull = ((g.nz + 1) / 2) / pk_pairs(NV, PkT<T>::CODE);
     const int S = pk_splits(p, b, s_count);
     a.part = S > 1 ? p->d_split : nullptr;
     a.part_stride = p->split_stride;

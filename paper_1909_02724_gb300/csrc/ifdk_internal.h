@@ -54,6 +54,10 @@ constexpr int kPkBoxS = 32, kPkBoxL = 48;   // box widths (elements) the kernel 
 constexpr int pk_pairs(int nv, int q_dtype) { return nv == 2 && q_dtype != IFDK_F16 ? 12 : 16; }
 // resident blocks per SM the packed kernel is built for (registers) and sized for (shared memory)
 constexpr int pk_blocks(int nv) { return nv == 2 ? 2 : 3; }
+// z pairs of the blocks after the full L-pair z-blocks (the volume's remainder)
+constexpr int kPkTailL = 4;
+// z-blocks of a packed launch: npairs / L full blocks, then tail blocks of kPkTailL pairs
+constexpr int pk_zblocks(int npairs, int L) { return npairs / L + (npairs % L + kPkTailL - 1) / kPkTailL; }
 // view split of the packed back-projection (small volumes): at most 16 partial
 // volumes of at most 64 MiB together, each part at least 2 pairs (or views)
 constexpr int kPkMaxSplits = 16, kPkSplitMinUnits = 2;

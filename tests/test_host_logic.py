@@ -167,6 +167,15 @@ def test_fold_windows_of_every_gpu_test_geometry(dtype):
 # hold every tap, and every tap row a written voxel reads is a packed row
 # unless both it and its mirror lie outside the detector (then 0 is right).
 
+TAIL_L = 4   # z pairs of the packed kernel's tail blocks
+
+
+def packed_zblocks(npairs, L):
+    """z-blocks of a packed launch: npairs // L blocks of L pairs, then the
+    remainder in blocks of TAIL_L pairs."""
+    return npairs // L + -(-(npairs % L) // TAIL_L)
+
+
 def check_packed_windows(g, q_dtype, view_pairing=True, blocks=None):
     info = B.ifdk_query_packed(g, q_dtype, view_pairing)
     if info["path"] == 0:
@@ -180,22 +189,26 @@ def check_packed_windows(g, q_dtype, view_pairing=True, blocks=None):
     ny_cols = g.ny // 2 if info["path"] == 2 else g.ny
     tiles_x, tiles_y = -(-g.nx // TILE), -(-ny_cols // TILE)
     npairs = (g.nz + 1) // 2
-    zblocks = -(-npairs // L)
+    zblocks = packed_zblocks(npairs, L)
     assert info["blocks"] == tiles_x * tiles_y * zblocks
     if blocks is None:
         blocks = [(bx, by, bz) for bx in range(tiles_x) for by in range(tiles_y) for bz in range(zblocks)]
     tx, ty = np.meshgrid(np.arange(TILE), np.arange(TILE), indexing="ij")
     tx, ty = tx.ravel(), ty.ravel()
-    p = np.arange(L)
+    zfull = npairs // L
     for bx, by, bz in blocks:
-        i0, j0, k0 = bx * TILE, by * TILE, bz * L
+        # full z-blocks of L pairs, then tail blocks of TAIL_L pairs
+        Lb = L if bz < zfull else TAIL_L
+        k0 = bz * L if bz < zfull else zfull * L + (bz - zfull) * TAIL_L
+        p = np.arange(Lb)
+        i0, j0 = bx * TILE, by * TILE
         kp0 = k0 - cz
         ia, ib, ja, jb = i0 - cx, i0 + TILE - 1 - cx, j0 - cy, j0 + TILE - 1 - cy
         ci, cj = np.array([ia, ib, ia, ib]), np.array([ja, ja, jb, jb])
         zc = t["C0"][:, None] * ci + t["C1"][:, None] * cj + t["C3"][:, None]
         ucn = (t["A0"][:, None] * ci + t["A1"][:, None] * cj) / zc
         u_lo, z_lo, z_hi = ucn.min(1), zc.min(1), zc.max(1)
-        e0, e1 = t["B2"] * kp0, t["B2"] * (kp0 + L - 1)
+        e0, e1 = t["B2"] * kp0, t["B2"] * (kp0 + Lb - 1)
         v_lo = np.minimum(np.minimum(e0 / z_lo, e0 / z_hi), np.minimum(e1 / z_lo, e1 / z_hi))
         u0a = np.floor((np.floor(uc + u_lo) - MARGIN + 1) / AL) * AL - 1
         # the TMA box starts at element u0a + 1: 4 values of q_dtype each, 16-byte aligned
@@ -260,7 +273,7 @@ def test_packed_windows_large_workloads(name):
             info = B.ifdk_query_packed(g, dt, pairing)
             ny_cols = g.ny // 2 if info["path"] == 2 else g.ny
             tx, ty = -(-g.nx // TILE), -(-ny_cols // TILE)
-            zb = -(-((g.nz + 1) // 2) // info["z_per_thread"])
+            zb = packed_zblocks((g.nz + 1) // 2, info["z_per_thread"])
             blocks = {(0, 0, 0), (tx - 1, ty - 1, zb - 1), (tx // 2, ty // 2, zb // 2), (0, ty - 1, 0),
                       (tx - 1, 0, zb - 1)}
             blocks |= {(int(rng.integers(tx)), int(rng.integers(ty)), int(rng.integers(zb))) for _ in range(6)}
