@@ -1,0 +1,33 @@
+"""Seeded random scanner geometries shared by the CPU window checks and the
+GPU parity sweep (geometry parameters only; no reconstruction arithmetic)."""
+import numpy as np
+
+from paper_1909_02724_gb300.geometry import circular
+
+
+def random_geometries(n=12, seed=2024):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nu = int(rng.integers(16, 72))
+        nv = int(rng.integers(12, 64))
+        du = float(rng.uniform(0.6, 1.8))
+        dv = float(rng.uniform(0.6, 1.8))
+        sid = float(rng.uniform(400.0, 1200.0))
+        sdd = sid * float(rng.uniform(1.2, 2.0))
+        nx, ny, nz = (int(rng.integers(4, 40)) for _ in range(3))
+        # voxels sized so that the volume stays inside the untruncated field of view
+        fov = 0.5 * min(nu * du, nv * dv) * sid / sdd
+        dx = float(rng.uniform(0.4, 1.0)) * fov / max(nx, ny, nz)
+        n_views = int(rng.integers(3, 40))
+        # half of them with offsets: a V offset of whole half pixels keeps 2 v_c integral
+        kw = {}
+        if i % 2:
+            kw["off_u"] = float(rng.uniform(-2.0, 2.0)) * du
+            kw["off_v"] = 0.5 * int(rng.integers(-6, 7)) * dv
+        if i % 4 == 3:
+            kw["vol_off_z"] = float(rng.uniform(-2.0, 2.0)) * dx
+        g = circular(n_views, nu, nv, du, dv, nx, ny, nz, dx, sid=sid, sdd=sdd,
+                     start=float(rng.uniform(0, 2 * np.pi)), **kw)
+        out.append((f"rand{i}", g))
+    return out

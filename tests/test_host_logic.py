@@ -319,3 +319,13 @@ def test_packed_path_needs_row_steps_below_two():
     g = circular(8, 64, 64, 0.5, 0.5, 16, 16, 16, 0.5, dz=0.5)
     assert B.ifdk_query_packed(g, B.IFDK_F32)["path"] in (1, 2)      # step ~1.5
     assert B.ifdk_query_packed(g.with_(dz=0.7), B.IFDK_F32)["path"] == 0   # step ~2.1
+
+
+def test_packed_windows_random_geometries():
+    """Every tap of every block and view lies in its window for the seeded random
+    geometries that the GPU parity sweep runs."""
+    from tests.random_geometries import random_geometries
+    for name, g in random_geometries():
+        for dt in (B.IFDK_F32, B.IFDK_F16):
+            for pairing in (True, False):
+                check_packed_windows(g, dt, pairing)
