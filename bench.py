@@ -220,6 +220,11 @@ def run_ours(args):
     from paper_1909_02724_gb300.parallel import max_over_ranks
     from paper_1909_02724_gb300.phantom import workload, workload_projections_gpu
 
+    # one rank compiles whatever is stale, the others wait and load its output
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
     build()
     w = workload(args.workload)
     g = w.geom
