@@ -18,8 +18,11 @@
  *   - View s rotates the object by +angles[s] about Z (Mrot); the source sits
  *     at (-d sin b, -d cos b, 0); pixel (iu, iv) is centred at index position,
  *     principal point ((nu-1)/2 + off_u/du, (nv-1)/2 + off_v/dv) (M1).
- *   - Ownership: the caller owns every data buffer and stream; a plan owns only
- *     its immutable geometry tables (and a device status word).
+ *   - Ownership: the caller owns every data buffer and stream.  A plan owns
+ *     its geometry tables (view terms, F_cos, taps, the filter's split tap
+ *     planes, the short-scan weights when set), a device status word, the
+ *     partial volumes of the view split (small volumes only) and, for
+ *     ifdk_backproject_host, a copy stream and events.
  *   - Asynchrony: filter / backproject / project enqueue kernels on `stream`
  *     (a cudaStream_t; NULL = the legacy default stream), allocate nothing,
  *     and do not synchronise.  Outputs of backproject / project ACCUMULATE:
@@ -30,8 +33,11 @@
  *     buffers untouched.  Nothing is thrown or printed.  Faults found on the
  *     device (a bounded wait that ran out) are latched in the plan's status
  *     word and reported by ifdk_last_device_status.
- *   - One plan is used by one host thread at a time; calls on one plan may be
- *     enqueued on any streams (the kernels only read the plan's tables).
+ *   - One plan is used by one host thread at a time.  Calls on one plan may be
+ *     enqueued on any streams, with two exceptions that must not overlap on
+ *     the device with another call of the same kind on the plan: packed
+ *     back-projections that use the view split (they share the plan's partial
+ *     volumes) and ifdk_backproject_host (it uses the plan's copy stream).
  */
 #ifndef IFDK_H
 #define IFDK_H
@@ -110,7 +116,9 @@ int ifdk_destroy(ifdk_plan p);
    ifdk_filter_workspace_size reports, 128-byte aligned, owned by the caller
    and not used by anything else until the call's work has run (larger
    workspaces process more rows per launch).  split_terms = 0: FP32 SIMT
-   kernel of the same sum by parts, workspace ignored (may be NULL). */
+   kernel of the same sum by parts, workspace ignored (may be NULL).
+   With ifdk_set_short_scan on, E is also weighted by 2 w(beta_s, gamma_m)
+   together with F_cos. */
 int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms,
                 void *workspace, size_t workspace_bytes, void *stream);
 
@@ -159,7 +167,8 @@ int ifdk_filter_noalloc(ifdk_plan p, const float *E, void *Q, int q_dtype, int s
 
 /* Adjoint of ifdk_filter for FP32 (the Toeplitz matrix is symmetric because h
    is even, and F_cos is diagonal): G_E[s][v][m] = F_cos[v][m] sum_n h(n-m) G_Q[s][v][n].
-   G_Q, G_E: device FP32 [np][nv][nu]; G_E is overwritten. */
+   G_Q, G_E: device FP32 [np][nv][nu]; G_E is overwritten.  With
+   ifdk_set_short_scan on, G_E is also weighted by 2 w(beta_s, gamma_m). */
 int ifdk_filter_adjoint(ifdk_plan p, const float *G_Q, float *G_E, void *stream);
 
 /* Back-projection, Algorithm 4: for every voxel and view s in
