@@ -1,6 +1,7 @@
 // Adjoint of the back-projection: the transpose of Algorithm 4 / Algorithm 3.
 // Every voxel value is splatted with weight w_s f^2 times its bilinear
-// coefficients onto the four taps of every view (FP32 atomics).  The per
+// coefficients onto the four taps of every view (FP32 atomics; a thread sums
+// the taps its z-run puts on the same detector row before the atomic).  The per
 // (column, view) terms are formed once and reused over the thread's z-run,
 // exactly as in the back-projection.
 #include "ifdk_device.cuh"
@@ -57,6 +58,13 @@ __global__ void __launch_bounds__(kThreads) project_kernel(const ProjArgs a)
         const float sig = t0.w * f;
         const float vb = fmaf(t1.x, f, a.vc);
         float *Ps = a.P + (size_t)s * a.nv * a.nu;
+        // v is monotonic along the z-run, so consecutive voxels share detector rows
+        // (one row per voxel at about one row per step): the taps of the two rows
+        // last touched, pr and pr + 1, stay in registers and a row goes out (two
+        // atomics) once no later voxel of the run can reach it
+        bool pending = false;
+        int pr = 0;
+        float q00 = 0.0f, q01 = 0.0f, q10 = 0.0f, q11 = 0.0f;   // row pr: q00, q01; row pr + 1: q10, q11
 #pragma unroll
         for (int z = 0; z < kProjZ; ++z) {
             const float v = fmaf((float)(kb + z) - a.cz, sig, vb);
@@ -66,10 +74,36 @@ __global__ void __launch_bounds__(kThreads) project_kernel(const ProjArgs a)
             const float dv = v - fv;
             const float wv = W * x[z];
             const float lo = wv * (1.0f - dv), hi = wv * dv;
-            splat(Ps, a.nu, a.nv, iu, iv, lo * (1.0f - du));
-            splat(Ps, a.nu, a.nv, iu + 1, iv, lo * du);
-            splat(Ps, a.nu, a.nv, iu, iv + 1, hi * (1.0f - du));
-            splat(Ps, a.nu, a.nv, iu + 1, iv + 1, hi * du);
+            const float a0 = lo * (1.0f - du), a1 = lo * du, b0 = hi * (1.0f - du), b1 = hi * du;
+            if (pending && iv == pr) {
+                q00 += a0; q01 += a1; q10 += b0; q11 += b1;
+            } else if (pending && iv == pr + 1) {
+                splat(Ps, a.nu, a.nv, iu, pr, q00);
+                splat(Ps, a.nu, a.nv, iu + 1, pr, q01);
+                q00 = q10 + a0; q01 = q11 + a1; q10 = b0; q11 = b1;
+                pr = iv;
+            } else if (pending && iv == pr - 1) {
+                splat(Ps, a.nu, a.nv, iu, pr + 1, q10);
+                splat(Ps, a.nu, a.nv, iu + 1, pr + 1, q11);
+                q10 = q00 + b0; q11 = q01 + b1; q00 = a0; q01 = a1;
+                pr = iv;
+            } else {
+                if (pending) {
+                    splat(Ps, a.nu, a.nv, iu, pr, q00);
+                    splat(Ps, a.nu, a.nv, iu + 1, pr, q01);
+                    splat(Ps, a.nu, a.nv, iu, pr + 1, q10);
+                    splat(Ps, a.nu, a.nv, iu + 1, pr + 1, q11);
+                }
+                q00 = a0; q01 = a1; q10 = b0; q11 = b1;
+                pr = iv;
+                pending = true;
+            }
+        }
+        if (pending) {
+            splat(Ps, a.nu, a.nv, iu, pr, q00);
+            splat(Ps, a.nu, a.nv, iu + 1, pr, q01);
+            splat(Ps, a.nu, a.nv, iu, pr + 1, q10);
+            splat(Ps, a.nu, a.nv, iu + 1, pr + 1, q11);
         }
     }
 }
