@@ -79,7 +79,9 @@ def reduce_volume(vol, dst: int = 0):
 
 def gather_slabs(slab_vol, full_vol=None, dst: int = 0, nz: int | None = None):
     """Collects the slabs of a row split on rank dst into full_vol [nx][ny][nz]
-    (k fastest), slab r holding k in split_range(nz, world, r)."""
+    (k fastest; made here when None), slab r holding k in split_range(nz, world, r).
+    Returns full_vol on dst (on the other ranks whatever they passed); nz is needed when no
+    rank passes full_vol."""
     import torch
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
@@ -89,6 +91,10 @@ def gather_slabs(slab_vol, full_vol=None, dst: int = 0, nz: int | None = None):
         return slab_vol
     world, rank = dist.get_world_size(), dist.get_rank()
     nz = full_vol.shape[2] if full_vol is not None else nz
+    if nz is None:
+        raise ValueError("gather_slabs needs full_vol or nz")
+    if rank == dst and full_vol is None:
+        full_vol = torch.empty(slab_vol.shape[:2] + (nz,), dtype=slab_vol.dtype, device=slab_vol.device)
     # gather wants equal shapes: every slab travels padded to the longest one
     kmax = split_range(nz, world, 0)[1]
     send = torch.zeros(slab_vol.shape[:2] + (kmax,), dtype=slab_vol.dtype, device=slab_vol.device)

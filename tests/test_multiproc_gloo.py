@@ -51,9 +51,13 @@ def _worker(rank, port, q):
         vs = torch.from_numpy(oracle.backproject(slab.geom, Q, threads=1))
         full = torch.zeros((g.nx, g.ny, g.nz), dtype=torch.float64) if rank == 0 else None
         P.gather_slabs(vs, full, dst=0, nz=g.nz)
+        made = P.gather_slabs(vs, None, dst=1, nz=g.nz)      # allocated on the destination rank
         if rank == 0:
             out["reduced"] = part.numpy()
             out["gathered"] = full.numpy()
+            assert made is None
+        else:
+            out["gathered_on_1"] = made.numpy()
         dist.barrier()
         dist.destroy_process_group()
         q.put(out)
@@ -148,3 +152,4 @@ def test_slab_split_gather_equals_single_process(results):
     got = results[0]["gathered"]
     # the slab's matrices differ from the volume's only in rounding (the Z shift)
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+    np.testing.assert_array_equal(results[1]["gathered_on_1"], got)
