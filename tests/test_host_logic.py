@@ -329,3 +329,27 @@ def test_packed_windows_random_geometries():
         for dt in (B.IFDK_F32, B.IFDK_F16):
             for pairing in (True, False):
                 check_packed_windows(g, dt, pairing)
+
+
+def test_every_entry_point_refuses_a_null_plan_before_any_cuda_call():
+    """With a NULL plan (or NULL outputs) every call returns IFDK_ERR_INVALID
+    without touching the device (this runs without a GPU); ifdk_destroy(NULL)
+    is a no-op."""
+    lib = B.load_library()
+    for name in B.EXPORTS:
+        if name in ("ifdk_status_string",):
+            continue
+        fn = getattr(lib, name)
+        args = []
+        for t in fn.argtypes:
+            if t in (ctypes.c_int, ctypes.c_int32):
+                args.append(0)
+            elif t in (ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int64):
+                args.append(0)
+            else:
+                args.append(None)
+        rc = fn(*args)
+        if name == "ifdk_destroy":
+            assert rc == B.IFDK_OK
+        else:
+            assert rc == B.IFDK_ERR_INVALID, (name, rc)
