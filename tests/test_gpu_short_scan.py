@@ -98,3 +98,18 @@ def test_short_scan_switch_and_refusals():
         with pytest.raises(IfdkError) as e:
             ifdk_set_short_scan(p.handle, True)
         assert e.value.code == IFDK_ERR_GEOMETRY, name
+
+
+@pytest.mark.parametrize("dtype,split", [(torch.float32, 3), (torch.float16, 2)])
+def test_short_scan_noalloc_filter_equals_workspace_filter(dtype, split):
+    from paper_1909_02724_gb300.binding import Plan, dtype_code, ifdk_filter_noalloc
+    g = GEOMS["short64"]
+    plan = Plan(g)
+    E = torch.from_numpy(phantom_E(g)).cuda()
+    want = plan.filter(E, dtype=dtype, split_terms=split)
+    got = torch.empty_like(want)
+    ifdk_filter_noalloc(plan.handle, E, got, dtype_code(dtype), split)
+    torch.cuda.synchronize()
+    # the same kernels on the same 128-row tiles, in launches of at most 16 MiB of operands
+    assert float((got.float() - want.float()).abs().max()) <= 1e-6 * float(want.float().abs().max())
+    assert torch.equal(got[0], torch.zeros_like(got[0]))       # the first view has weight 0
