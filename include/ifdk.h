@@ -82,7 +82,9 @@ enum {
     IFDK_ERR_CUDA = -4,         /* a CUDA runtime call failed (no device, launch error) */
     IFDK_ERR_TIMEOUT = -5,      /* a bounded device wait ran out (device status) */
     IFDK_ERR_NOMEM = -6,        /* ifdk_create could not allocate its tables */
-    IFDK_ERR_UNSUPPORTED = -7   /* valid request the library does not implement */
+    IFDK_ERR_UNSUPPORTED = -7,  /* valid request the library does not implement */
+    IFDK_ERR_BOUNDS = -8        /* device status of a checked build (compiled with
+                                   IFDK_CHECK): a kernel read outside its window */
 };
 
 /* Builds a plan: FP64 per-view projection terms P_s = (M1 . Mrot(b_s) . M0)[0:3]

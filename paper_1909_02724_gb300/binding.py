@@ -16,13 +16,14 @@ import threading
 from .geometry import Geometry
 
 _LIBDIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib")
-LIB_PATH = os.path.join(_LIBDIR, "libifdk.so")
+# IFDK_LIB_PATH selects another build of the same C-ABI (the checked build in tests)
+LIB_PATH = os.environ.get("IFDK_LIB_PATH") or os.path.join(_LIBDIR, "libifdk.so")
 
 IFDK_F32, IFDK_F16, IFDK_BF16 = 0, 1, 2
 _ELEM = {0: 4, 1: 2, 2: 2}   # bytes per element of each storage type
 IFDK_OK = 0
 IFDK_ERR_INVALID, IFDK_ERR_GEOMETRY, IFDK_ERR_ALIGNMENT, IFDK_ERR_CUDA = -1, -2, -3, -4
-IFDK_ERR_TIMEOUT, IFDK_ERR_NOMEM, IFDK_ERR_UNSUPPORTED = -5, -6, -7
+IFDK_ERR_TIMEOUT, IFDK_ERR_NOMEM, IFDK_ERR_UNSUPPORTED, IFDK_ERR_BOUNDS = -5, -6, -7, -8
 
 # every symbol include/ifdk.h declares
 EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_size", "ifdk_filter_noalloc",

@@ -17,6 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(LIBDIR, "libifdk.so")
+CHECK_LIB = os.path.join(LIBDIR, "libifdk_check.so")   # the checked build (IFDK_CHECK)
 PHANTOM_LIB = os.path.join(LIBDIR, "libifdk_phantom.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -61,6 +62,28 @@ def _link(objs: list[str], out: str) -> None:
     if r.returncode != 0:
         raise RuntimeError(f"link failed for {os.path.basename(out)}:\n{r.stderr}")
     os.replace(tmp, out)
+
+
+def build_checked(force: bool = False) -> str:
+    """The library compiled with -DIFDK_CHECK (window-bounds checks on every tap read
+    of the packed back-projector; a miss sets the plan's status to IFDK_ERR_BOUNDS),
+    for tests.  Its objects sit beside the normal ones with a _check suffix."""
+    os.makedirs(LIBDIR, exist_ok=True)
+    headers = _headers()
+    objs, jobs = [], []
+    for s in LIB_SOURCES:
+        src = os.path.join(CSRC, s)
+        obj = os.path.join(LIBDIR, s.replace(".cu", "_check.o"))
+        objs.append(obj)
+        if force or _stale(obj, [src, *headers]):
+            jobs.append((src, obj))
+    if jobs:
+        with ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+            for f in [ex.submit(_compile, s, o, ["-DIFDK_CHECK"]) for s, o in jobs]:
+                f.result()
+    if force or _stale(CHECK_LIB, objs):
+        _link(objs, CHECK_LIB)
+    return CHECK_LIB
 
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> list[str]:

@@ -250,10 +250,36 @@ template <> struct Tap<__nv_bfloat16> {
 // less shared-memory traffic, for FP32 taps); ANY loads both rows.
 enum class Reuse { STEP1, STEP2, ANY };
 
+// Checked build (-DIFDK_CHECK): every tap read is tested against the stage's box;
+// a read outside it sets kStatusBounds in the plan's status word and reads the
+// box's first element instead.  Without the flag the macros add nothing.
+#ifdef IFDK_CHECK
+struct ChkBox {
+    const unsigned char *lo, *hi;
+    unsigned int *status;
+};
+template <typename T>
+__device__ __forceinline__ const unsigned char *chk_row(const unsigned char *e, const ChkBox &c)
+{
+    if (e < c.lo || e + Tap<T>::ES > c.hi) {
+        atomicOr(c.status, kStatusBounds);
+        return c.lo;
+    }
+    return e;
+}
+#define PK_CHK_PARAM , const ChkBox &chk
+#define PK_CHK_ARG , chk
+#define PK_ROW(ptr) Tap<T>::row(chk_row<T>((ptr), chk), du2, duh)
+#else
+#define PK_CHK_PARAM
+#define PK_CHK_ARG
+#define PK_ROW(ptr) Tap<T>::row((ptr), du2, duh)
+#endif
+
 template <typename T, int NV, int L, uint32_t ROWB, uint32_t HB, Reuse MODE>
 __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], const unsigned char *sm,
                                           uint32_t base, float sig, float vb, float2 du2, __half2 duh,
-                                          typename Tap<T>::Wt W0, typename Tap<T>::Wt W1)
+                                          typename Tap<T>::Wt W0, typename Tap<T>::Wt W1 PK_CHK_PARAM)
 {
     using R = typename Tap<T>::R;
     R lo[NV], hi[NV];
@@ -262,8 +288,8 @@ __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], cons
     const unsigned char *e = sm + (base + tv * ROWB);   // 32-bit offset arithmetic wraps the biases away
 #pragma unroll
     for (int n = 0; n < NV; ++n) {
-        lo[n] = Tap<T>::row(e + n * HB, du2, duh);
-        hi[n] = Tap<T>::row(e + ROWB + n * HB, du2, duh);
+        lo[n] = PK_ROW(e + n * HB);
+        hi[n] = PK_ROW(e + ROWB + n * HB);
     }
     a0[0] = Tap<T>::accum(a0[0], lo[0], hi[0], make_float2(dv, dv), __float2half2_rn(dv), W0);
     if constexpr (NV == 2) a1[0] = Tap<T>::accum(a1[0], lo[1], hi[1], make_float2(dv, dv), __float2half2_rn(dv), W1);
@@ -276,15 +302,15 @@ __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], cons
         if constexpr (MODE == Reuse::ANY) {
 #pragma unroll
             for (int n = 0; n < NV; ++n) {
-                lo[n] = Tap<T>::row(e + n * HB, du2, duh);
-                hi[n] = Tap<T>::row(e + ROWB + n * HB, du2, duh);
+                lo[n] = PK_ROW(e + n * HB);
+                hi[n] = PK_ROW(e + ROWB + n * HB);
             }
         } else if constexpr (MODE == Reuse::STEP1) {
             const bool moved = tn != tv;
             tv = tn;
 #pragma unroll
             for (int n = 0; n < NV; ++n) {
-                const R hn = Tap<T>::row(e + ROWB + n * HB, du2, duh);
+                const R hn = PK_ROW(e + ROWB + n * HB);
                 lo[n] = moved ? hi[n] : lo[n];
                 hi[n] = hn;
             }
@@ -293,9 +319,9 @@ __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], cons
             tv = tn;
 #pragma unroll
             for (int n = 0; n < NV; ++n) {
-                const R hn = Tap<T>::row(e + ROWB + n * HB, du2, duh);
+                const R hn = PK_ROW(e + ROWB + n * HB);
                 R ln = step != 0 ? hi[n] : lo[n];
-                if (step == 2) ln = Tap<T>::row(e + n * HB, du2, duh);
+                if (step == 2) ln = PK_ROW(e + n * HB);
                 lo[n] = ln;
                 hi[n] = hn;
             }
@@ -491,10 +517,13 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
         // (FP32 taps keep the reuse across two-row steps; 16-bit taps load both rows,
         // which measured faster for them)
         constexpr Reuse WIDE = sizeof(T) == 4 ? Reuse::STEP2 : Reuse::ANY;
+#ifdef IFDK_CHECK
+        const ChkBox chk{sm + sg + kPkBox, sm + sg + kPkBox + a.box_tx_bytes, a.status};
+#endif
         if (__all_sync(0xffffffffu, sig < 0.9990234375f))
-            pair_loop<T, NV, L, ROWB, HB, Reuse::STEP1>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1);
+            pair_loop<T, NV, L, ROWB, HB, Reuse::STEP1>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1 PK_CHK_ARG);
         else
-            pair_loop<T, NV, L, ROWB, HB, WIDE>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1);
+            pair_loop<T, NV, L, ROWB, HB, WIDE>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1 PK_CHK_ARG);
         __syncwarp();
         if (lane == 0) mbar_arrive(s0 + kPkEmpty + 8u * st);
     };

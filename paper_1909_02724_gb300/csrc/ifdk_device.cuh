@@ -12,6 +12,7 @@ namespace ifdk {
 
 // Bits of the device status word.
 constexpr unsigned kStatusTimeout = 1u;
+constexpr unsigned kStatusBounds = 2u;    // a checked build (IFDK_CHECK) caught an access outside its window
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {

@@ -145,6 +145,7 @@ const char *ifdk_status_string(int code)
     case IFDK_ERR_TIMEOUT: return "bounded device wait ran out";
     case IFDK_ERR_NOMEM: return "out of memory";
     case IFDK_ERR_UNSUPPORTED: return "unsupported request";
+    case IFDK_ERR_BOUNDS: return "checked build: access outside a kernel's window";
     default: return "unknown status";
     }
 }
@@ -449,6 +450,7 @@ int ifdk_last_device_status(ifdk_plan p, void *stream)
         cudaStreamSynchronize(s) != cudaSuccess)
         return IFDK_ERR_CUDA;
     if (h & kStatusTimeout) return IFDK_ERR_TIMEOUT;
+    if (h & kStatusBounds) return IFDK_ERR_BOUNDS;
     return IFDK_OK;
 }
 
