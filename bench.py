@@ -379,7 +379,8 @@ def run_ours(args):
                        if packed else "filtered views as stored",
                        "bp_launch": info, "view_split": splits},
             "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roofline,
-            "cpu_baseline": cpu, "output_stage": output_stage}
+            "cpu_baseline": cpu, "output_stage": output_stage,
+            "value_1e9": value * 2 ** 30 / 1e9}   # the same throughput in 10^9 updates/s
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
