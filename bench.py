@@ -125,20 +125,17 @@ def measured_peaks():
         return {}
 
 
-def profile_traffic(kernel_file: str, prof: str):
-    """DRAM bytes per launch of the back-projection kernel from the committed ncu
-    summary profiles/<prof>.json, if it was taken on the current kernel source
-    (else None)."""
+def profile_record(kernel_file: str, prof: str) -> dict:
+    """The committed ncu summary profiles/<prof>.json of the back-projection kernel,
+    if it was taken on the current kernel source (else {})."""
     path = os.path.join(ROOT, "profiles", f"{prof}.json")
     try:
         with open(path) as f:
-            prof = json.load(f)
+            rec = json.load(f)
         src = open(os.path.join(ROOT, "paper_1909_02724_gb300", "csrc", kernel_file), "rb").read()
-        if prof.get("source_sha1") != hashlib.sha1(src).hexdigest():
-            return None
-        return prof.get("dram_bytes_per_launch")
+        return rec if rec.get("source_sha1") == hashlib.sha1(src).hexdigest() else {}
     except (OSError, ValueError):
-        return None
+        return {}
 
 
 def oracle_sample_fdk(w, E_rows_fn, n_slices: int, threads: int):
@@ -349,8 +346,10 @@ def run_ours(args):
     else:
         kname = "bp_pairs_fold_kernel" if info["path"] == 1 else "bp_general_kernel"
         kfile, prof = "ifdk_bp.cu", f"bp_fold_{args.workload}"
+    rec = profile_record(kfile, prof)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gups, "unit": UNIT,
-                "frac": achieved / peak_gups, "traffic": profile_traffic(kfile, prof),
+                "frac": achieved / peak_gups, "traffic": rec.get("dram_bytes_per_launch"),
+                "ncu": rec.get("ncu"),   # the binding counters of that capture (profiles/<prof>.md)
                 "kernel": kname,
                 "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz (MEASURED_PEAKS sm_max_mhz) "
                               f"/ {FP32_OPS_PER_UPDATE} FP32 ops per update",
