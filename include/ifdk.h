@@ -248,6 +248,21 @@ int ifdk_backproject_packed(ifdk_plan p, const void *Qp, int q_dtype, int view_b
    enable = 0 turns pairing off for this plan, 1 back on. */
 int ifdk_set_view_pairing(ifdk_plan p, int enable);
 
+/* ifdk_backproject_packed for the mirror pairs k in [pair_begin, pair_begin +
+   pair_count) of the volume only (k < (nz+1)/2 pairs voxel k with nz-1-k): the
+   paper's sub-volumes, a z-slab together with its mirror slab, which Theorem 1
+   serves from the same view rows (Sec. 4 splits the volume into such pairs
+   over the rows of its worker grid; each needs every view and no collective).
+   vol: device FP32 [nx][ny][nz_out], 16-byte aligned, ACCUMULATED into, with
+   nz_out = 2 pair_count (2 pair_count - 1 when nz is odd and the range holds
+   the middle slice, which is its own mirror): voxel k of the volume is
+   vol[..][k - pair_begin] and its mirror nz-1-k is vol[..][nz_out-1-(k - pair_begin)].
+   Qp as for ifdk_backproject_packed (all np packed views).  The arithmetic per
+   voxel is that of the whole-volume call.  Returns IFDK_ERR_INVALID for a
+   range outside [0, (nz+1)/2). */
+int ifdk_backproject_packed_pairs(ifdk_plan p, const void *Qp, int q_dtype, int view_begin, int view_count,
+                                  int pair_begin, int pair_count, float *vol, void *stream);
+
 /* Describes a full-range ifdk_backproject_packed launch with q_dtype:
    info[0] = path (2 = half-turn view pairs, 1 = single views, 0 = packed
    path not available), info[1] = TMA box width (elements), info[2] = box

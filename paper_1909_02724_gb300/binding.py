@@ -33,7 +33,8 @@ EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_
            "ifdk_backproject_info", "ifdk_query_backproject", "ifdk_query_rows", "ifdk_status_string",
            "ifdk_packed_size", "ifdk_pack_views", "ifdk_backproject_packed", "ifdk_set_view_pairing",
            "ifdk_backproject_packed_info", "ifdk_query_packed", "ifdk_volume_slices",
-           "ifdk_set_view_split", "ifdk_view_split", "ifdk_filter_max", "ifdk_set_short_scan")
+           "ifdk_set_view_split", "ifdk_view_split", "ifdk_filter_max", "ifdk_set_short_scan",
+           "ifdk_backproject_packed_pairs")
 
 
 class IfdkError(RuntimeError):
@@ -100,6 +101,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.ifdk_volume_slices.argtypes = [vp, vp, vp, i32, i32, i32, vp]
         lib.ifdk_set_view_split.argtypes = [vp, i32]
         lib.ifdk_set_short_scan.argtypes = [vp, i32]
+        lib.ifdk_backproject_packed_pairs.argtypes = [vp, vp, i32, i32, i32, i32, i32, vp, vp]
         lib.ifdk_view_split.argtypes = [vp, i32, ctypes.POINTER(i32)]
         lib.ifdk_status_string.argtypes = [i32]
         lib.ifdk_status_string.restype = ctypes.c_char_p
@@ -247,6 +249,21 @@ def ifdk_backproject_packed(plan: int, Qp, q_dtype: int, view_begin: int, view_c
                             stream=None) -> None:
     _check(load_library().ifdk_backproject_packed(plan, _addr(Qp), int(q_dtype), int(view_begin), int(view_count),
                                                   _addr(vol), _stream(stream)), "ifdk_backproject_packed")
+
+
+def ifdk_backproject_packed_pairs(plan: int, Qp, q_dtype: int, view_begin: int, view_count: int, pair_begin: int,
+                                  pair_count: int, vol, stream=None) -> None:
+    _check(load_library().ifdk_backproject_packed_pairs(plan, _addr(Qp), int(q_dtype), int(view_begin),
+                                                        int(view_count), int(pair_begin), int(pair_count),
+                                                        _addr(vol), _stream(stream)),
+           "ifdk_backproject_packed_pairs")
+
+
+def pair_slab_depth(nz: int, pair_begin: int, pair_count: int) -> int:
+    """nz_out of a pair-range volume: 2 pair_count, less the middle slice of an odd
+    nz (its own mirror) when the range holds it."""
+    npairs = (nz + 1) // 2
+    return 2 * pair_count - (1 if nz % 2 and pair_begin + pair_count == npairs and pair_count > 0 else 0)
 
 
 def ifdk_set_view_pairing(plan: int, enable: bool) -> None:
@@ -500,6 +517,25 @@ class Plan:
         self._check_vol(vol)
         n = g.np - view_begin if view_count is None else view_count
         ifdk_backproject_packed(self.handle, Qp, dtype_code(Qp.dtype), view_begin, n, vol, stream)
+        return vol
+
+    def backproject_packed_pairs(self, Qp, pair_begin: int, pair_count: int, vol=None, view_begin: int = 0,
+                                 view_count: int | None = None, stream=None):
+        """Mirror pairs [pair_begin, pair_begin + pair_count) only (ifdk_backproject_packed_pairs):
+        vol [nx][ny][nz_out] holds the direct slab, then its mirror."""
+        import torch
+        g = self.geom
+        if not Qp.is_cuda or not Qp.is_contiguous() or tuple(Qp.shape) != self.packed_shape(Qp.dtype):
+            raise ValueError(f"Qp must be a contiguous CUDA tensor of shape {self.packed_shape(Qp.dtype)}")
+        nz_out = pair_slab_depth(g.nz, pair_begin, pair_count)
+        if vol is None:
+            vol = torch.zeros((g.nx, g.ny, nz_out), dtype=torch.float32, device=Qp.device)
+        if (not vol.is_cuda or not vol.is_contiguous() or vol.dtype != torch.float32
+                or tuple(vol.shape) != (g.nx, g.ny, nz_out)):
+            raise ValueError(f"vol must be a contiguous float32 CUDA tensor of shape {(g.nx, g.ny, nz_out)}")
+        n = g.np - view_begin if view_count is None else view_count
+        ifdk_backproject_packed_pairs(self.handle, Qp, dtype_code(Qp.dtype), view_begin, n, pair_begin, pair_count,
+                                      vol, stream)
         return vol
 
     def set_view_pairing(self, enable: bool) -> None:

@@ -86,6 +86,10 @@ struct PkArgs {
     size_t part_stride;
     int splits;
     int zfull;                          // z-blocks of L pairs; the rest take kPkTailL pairs
+    // mirror pairs [pair0, pair_end) of the volume go to an output column of nz_out
+    // voxels: the direct slab first (k - pair0), then its mirror (the whole volume:
+    // pair0 = 0, pair_end = (nz + 1) / 2, nz_out = nz)
+    int pair0, pair_end, nz_out;
 };
 
 template <typename T> struct PkT;
@@ -333,15 +337,19 @@ __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], cons
 
 // Writes a z-run: acc[p].x -> voxel k0+p, acc[p].y -> its mirror nz-1-k0-p, of column (i, j)
 // of the volume at dst: added (ADD), or stored (a partial volume of a view split).
-template <int L, bool ADD>
+// GEN (general launches: pair ranges, view split): the output column holds
+// nz_out voxels from pair pair0 on; else the whole volume (pair0 = 0, nz_out = nz).
+template <int L, bool ADD, bool GEN>
 __device__ __forceinline__ void write_run(const PkArgs &a, float *dst, int k0, int i, int j, const float2 *acc)
 {
     static_assert(L % 4 == 0, "the vector path stores float4 runs from k0 = a multiple of L");
-    float *col = dst + ((size_t)i * a.ny + j) * (size_t)a.nz;
-    const int half = a.nz / 2, npairs = (a.nz + 1) / 2;
-    if ((a.nz & 3) == 0 && k0 + L <= half) {
-        float4 *pd = reinterpret_cast<float4 *>(col + k0);
-        float4 *pm = reinterpret_cast<float4 *>(col + (a.nz - k0 - L));
+    const int nz_out = GEN ? a.nz_out : a.nz, pair0 = GEN ? a.pair0 : 0;
+    const int pair_end = GEN ? a.pair_end : (a.nz + 1) / 2;
+    float *col = dst + ((size_t)i * a.ny + j) * (size_t)nz_out;
+    const int lo = k0 - pair0;          // the run's first voxel in the output column
+    if ((nz_out & 3) == 0 && (lo & 3) == 0 && k0 + L <= min(a.nz / 2, pair_end)) {
+        float4 *pd = reinterpret_cast<float4 *>(col + lo);
+        float4 *pm = reinterpret_cast<float4 *>(col + (nz_out - lo - L));
 #pragma unroll
         for (int q = 0; q < L / 4; ++q) {
             float4 d = ADD ? pd[q] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -356,10 +364,10 @@ __device__ __forceinline__ void write_run(const PkArgs &a, float *dst, int k0, i
 #pragma unroll
         for (int p = 0; p < L; ++p) {
             const int k = k0 + p;
-            if (k < npairs) {
-                col[k] = ADD ? col[k] + acc[p].x : acc[p].x;
-                const int km = a.nz - 1 - k;
-                if (km > k) col[km] = ADD ? col[km] + acc[p].y : acc[p].y;
+            if (k < pair_end) {
+                const int kd = k - pair0, km = nz_out - 1 - kd;   // voxel k and its mirror nz - 1 - k
+                col[kd] = ADD ? col[kd] + acc[p].x : acc[p].x;
+                if (a.nz - 1 - k > k) col[km] = ADD ? col[km] + acc[p].y : acc[p].y;
             }
         }
     }
@@ -372,8 +380,9 @@ __device__ __forceinline__ void write_run(const PkArgs &a, float *dst, int k0, i
 constexpr uint32_t kPkFull = 0, kPkEmpty = 64, kPkAbort = 128, kPkLast = 160, kPkStage0 = 256, kPkBox = 128;
 static_assert(kPkMaxStages * 8 <= 64 && kPkLast + 4 * kPkMaxStages <= kPkStage0, "shared-memory map");
 
-// SPLIT: the launch splits its view range over grid layers (a.part != nullptr);
-// a separate instantiation keeps the whole-range kernel free of it.
+// SPLIT: the general instantiation, for launches that split their view range
+// over grid layers (a.part != nullptr) or cover a range of mirror pairs; a
+// separate instantiation keeps the whole-volume kernel free of both.
 // One block's work: the z-run of L pairs from pair k0 of a 16 x 16 column tile.
 template <typename T, int NV, int BW, int L, bool SPLIT>
 __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tmap, const int k0)
@@ -556,12 +565,15 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
     }
     if (ci < a.nx && cj < a.ny_cols) {
         if constexpr (!SPLIT) {
-            write_run<L, true>(a, a.vol, k0, ci, cj, acc[0]);
-            if constexpr (NV == 2) write_run<L, true>(a, a.vol, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
-        } else {
+            write_run<L, true, false>(a, a.vol, k0, ci, cj, acc[0]);
+            if constexpr (NV == 2) write_run<L, true, false>(a, a.vol, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
+        } else if (a.part != nullptr) {
             float *dst = a.part + blockIdx.z * a.part_stride;
-            write_run<L, false>(a, dst, k0, ci, cj, acc[0]);
-            if constexpr (NV == 2) write_run<L, false>(a, dst, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
+            write_run<L, false, true>(a, dst, k0, ci, cj, acc[0]);
+            if constexpr (NV == 2) write_run<L, false, true>(a, dst, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
+        } else {
+            write_run<L, true, true>(a, a.vol, k0, ci, cj, acc[0]);
+            if constexpr (NV == 2) write_run<L, true, true>(a, a.vol, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
         }
     }
 }
@@ -573,13 +585,14 @@ template <typename T, int NV, int BW, int L, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, pk_blocks(NV))
     bp_packed_kernel(const PkArgs a, const __grid_constant__ CUtensorMap tmap)
 {
+    const int pair0 = SPLIT ? a.pair0 : 0;
     if constexpr (L == kPkTailL) {
-        pk_block<T, NV, BW, L, SPLIT>(a, tmap, (int)blockIdx.y * L);
+        pk_block<T, NV, BW, L, SPLIT>(a, tmap, pair0 + (int)blockIdx.y * L);
     } else {
         if ((int)blockIdx.y < a.zfull)
-            pk_block<T, NV, BW, L, SPLIT>(a, tmap, (int)blockIdx.y * L);
+            pk_block<T, NV, BW, L, SPLIT>(a, tmap, pair0 + (int)blockIdx.y * L);
         else
-            pk_block<T, NV, BW, kPkTailL, SPLIT>(a, tmap, a.zfull * L + ((int)blockIdx.y - a.zfull) * kPkTailL);
+            pk_block<T, NV, BW, kPkTailL, SPLIT>(a, tmap, pair0 + a.zfull * L + ((int)blockIdx.y - a.zfull) * kPkTailL);
     }
 }
 
@@ -646,10 +659,10 @@ __global__ void __launch_bounds__(256) split_reduce_kernel(float *vol, const flo
 // Parts of the view range per launch: enough to fill one wave of the GPU when
 // the grid alone covers at most half of it, each part at least kPkSplitMinUnits
 // pairs (or views), at most the partial volumes the plan holds.
-int pk_splits(const ifdk_plan_s *p, const PkLaunch &b, int units)
+int pk_splits(const ifdk_plan_s *p, const PkLaunch &b, int units, int grid_y)
 {
     if (!p->d_split || p->view_split_max == 1) return 1;
-    const long long blocks = (long long)b.grid_x * b.grid_y, want = (long long)p->n_sm * pk_blocks(b.nv);
+    const long long blocks = (long long)b.grid_x * grid_y, want = (long long)p->n_sm * pk_blocks(b.nv);
     if (blocks * 2 > want) return 1;
     long long S = std::min<long long>((want + blocks - 1) / blocks, p->split_cap);
     if (p->view_split_max >= 2) S = std::min<long long>(S, p->view_split_max);
@@ -669,7 +682,7 @@ PkLaunch size_packed(const ifdk_plan_s *p, int q_dtype, int nv)
     b.align = q_dtype == IFDK_F32 ? 1 : 2;
     const int ny_cols = nv == 2 ? g.ny / 2 : g.ny;
     const int tiles_x = (g.nx + kTileX - 1) / kTileX, tiles_y = (ny_cols + kTileY - 1) / kTileY;
-    const int L = pk_pairs(nv, q_dtype), npairs = (g.nz + 1) / 2, zblocks = (npairs + L - 1) / L;
+    const int L = pk_pairs(nv, q_dtype), npairs = (g.nz + 1) / 2;
     b.grid_x = tiles_x * tiles_y;
     b.grid_y = pk_zblocks(npairs, L);
     if (!p->fold_ok) return b;
@@ -682,7 +695,8 @@ PkLaunch size_packed(const ifdk_plan_s *p, int q_dtype, int nv)
     if (cmin < 0.1 * g.sid) return b;
     const double et = std::hypot((kTileX - 1) * g.dx, (kTileY - 1) * g.dy);
     const double wu = g.sdd / g.du * et * (1.0 / cmin + 2.0 * rxy / (cmin * cmin));
-    const double kmax = std::max(cz, (double)zblocks * L - 1 - cz);
+    // a block may start at any pair (pair-range launches) and run L pairs on
+    const double kmax = std::max(cz, (double)(npairs + L - 2) - cz);
     const double b2 = g.sdd * g.dz / g.dv;
     if (b2 / cmin >= 1.9) return b;   // rows per voxel step (the largest sig) below 2
     const double hv = b2 * (L - 1) / cmin + b2 * kmax * et / (cmin * cmin);
@@ -708,7 +722,7 @@ PkLaunch size_packed(const ifdk_plan_s *p, int q_dtype, int nv)
 
 template <typename T, int NV, int BW>
 int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_begin, int s_count, int q_view0,
-                    int q_pair_off, int q_views, float *vol, cudaStream_t stream)
+                    int q_pair_off, int q_views, float *vol, cudaStream_t stream, const PkZRange &zr)
 {
     const ifdk_geometry &g = p->g;
     EncodeTiledFn enc = encode_tiled();
@@ -757,20 +771,27 @@ int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_beg
     a.wunscale = 1.0f / a.wscale;
     a.stage_bytes = (uint32_t)b.stage_bytes;
     a.box_tx_bytes = (uint32_t)((size_t)b.box_h * NV * BW * 4 * es);
-    a.zfull = ((g.nz + 1) / 2) / pk_pairs(NV, PkT<T>::CODE);
-    const int S = pk_splits(p, b, s_count);
+    constexpr int L = pk_pairs(NV, PkT<T>::CODE);
+    const int npairs = (g.nz + 1) / 2, pcount = zr.pcount < 0 ? npairs : zr.pcount;
+    a.pair0 = zr.pcount < 0 ? 0 : zr.pair0;
+    a.pair_end = a.pair0 + pcount;
+    a.nz_out = zr.pcount < 0 ? g.nz : zr.nz_out;
+    a.zfull = pcount / L;
+    const int grid_y = pk_zblocks(pcount, L);
+    if (grid_y == 0) return IFDK_OK;
+    const int S = pk_splits(p, b, s_count, grid_y);
     a.part = S > 1 ? p->d_split : nullptr;
     a.part_stride = p->split_stride;
     a.splits = S;
-    constexpr int L = pk_pairs(NV, PkT<T>::CODE);
+    const bool general = S > 1 || zr.pcount >= 0;
     void (*kern)(const PkArgs, const CUtensorMap) =
-        S > 1 ? bp_packed_kernel<T, NV, BW, L, true> : bp_packed_kernel<T, NV, BW, L, false>;
+        general ? bp_packed_kernel<T, NV, BW, L, true> : bp_packed_kernel<T, NV, BW, L, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem) != cudaSuccess)
         return IFDK_ERR_CUDA;
-    kern<<<dim3(b.grid_x, b.grid_y, S), kThreads, b.smem, stream>>>(a, tmap);
+    kern<<<dim3(b.grid_x, grid_y, S), kThreads, b.smem, stream>>>(a, tmap);
     if (cudaGetLastError() != cudaSuccess) return IFDK_ERR_CUDA;
     if (S > 1) {
-        const size_t n = (size_t)g.nx * g.ny * g.nz;
+        const size_t n = (size_t)g.nx * g.ny * a.nz_out;
         const size_t blocks = std::min<size_t>((n / 4 + 255) / 256 + 1, (size_t)p->n_sm * 8);
         split_reduce_kernel<<<(unsigned)blocks, 256, 0, stream>>>(vol, p->d_split, n, p->split_stride, S);
         if (cudaGetLastError() != cudaSuccess) return IFDK_ERR_CUDA;
@@ -780,28 +801,29 @@ int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_beg
 
 template <typename T, int NV>
 int launch_packed_bw(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_begin, int s_count, int q_view0,
-                     int q_pair_off, int q_views, float *vol, cudaStream_t stream)
+                     int q_pair_off, int q_views, float *vol, cudaStream_t stream, const PkZRange &zr)
 {
-    return b.bw == kPkBoxS
-               ? launch_packed_t<T, NV, kPkBoxS>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream)
-               : launch_packed_t<T, NV, kPkBoxL>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream);
+    return b.bw == kPkBoxS ? launch_packed_t<T, NV, kPkBoxS>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views,
+                                                             vol, stream, zr)
+                           : launch_packed_t<T, NV, kPkBoxL>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views,
+                                                             vol, stream, zr);
 }
 
 template <int NV>
 int launch_packed(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin, int s_count, int q_view0, int q_pair_off,
-                  int q_views, float *vol, cudaStream_t stream)
+                  int q_views, float *vol, cudaStream_t stream, const PkZRange &zr)
 {
     if (s_count <= 0) return IFDK_OK;
     const PkLaunch &b = NV == 2 ? p->pk2[q_dtype] : p->pk[q_dtype];
     if (!b.path) return IFDK_ERR_UNSUPPORTED;
     switch (q_dtype) {
     case IFDK_F32:
-        return launch_packed_bw<float, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream);
+        return launch_packed_bw<float, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream, zr);
     case IFDK_F16:
-        return launch_packed_bw<__half, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream);
+        return launch_packed_bw<__half, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream, zr);
     default:
         return launch_packed_bw<__nv_bfloat16, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol,
-                                                   stream);
+                                                   stream, zr);
     }
 }
 
@@ -832,7 +854,7 @@ int plan_view_split(ifdk_plan_s *p)
 int packed_view_split(const ifdk_plan_s *p, int q_dtype, int units, bool pairs)
 {
     const PkLaunch &b = pairs ? p->pk2[q_dtype] : p->pk[q_dtype];
-    return b.path ? pk_splits(p, b, units) : 1;
+    return b.path ? pk_splits(p, b, units, b.grid_y) : 1;
 }
 
 void split_half_turn(int np, int b, int e, int *m)
@@ -899,22 +921,22 @@ int launch_pack(ifdk_plan_s *p, const void *Q, int q_dtype, int n_views, void *Q
 int launch_packed_pairs(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin, int s_count, int q_view0,
                         int q_pair_off, int q_views, float *vol, cudaStream_t stream)
 {
-    return launch_packed<2>(p, Qp, q_dtype, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream);
+    return launch_packed<2>(p, Qp, q_dtype, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream, PkZRange{});
 }
 
 int launch_backproject_packed(ifdk_plan_s *p, const void *Qp, int q_dtype, int view_begin, int view_count,
-                              int q_view0, int q_views, float *vol, cudaStream_t stream)
+                              int q_view0, int q_views, float *vol, cudaStream_t stream, const PkZRange &zr)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return IFDK_ERR_CUDA;
     const int b = view_begin, e = view_begin + view_count, h = p->g.np / 2;
     int m = b;
     if (p->use_half_turn && p->pk2[q_dtype].path) split_half_turn(p->g.np, b, e, &m);
-    if (m == b) return launch_packed<1>(p, Qp, q_dtype, b, view_count, q_view0, 0, q_views, vol, stream);
+    if (m == b) return launch_packed<1>(p, Qp, q_dtype, b, view_count, q_view0, 0, q_views, vol, stream, zr);
     // views s in [b, m) with their partners s + h; then the unpaired [m, b + h) and [m + h, e)
-    int rc = launch_packed<2>(p, Qp, q_dtype, b, m - b, q_view0, h, q_views, vol, stream);
-    if (rc == IFDK_OK) rc = launch_packed<1>(p, Qp, q_dtype, m, b + h - m, q_view0, 0, q_views, vol, stream);
-    if (rc == IFDK_OK) rc = launch_packed<1>(p, Qp, q_dtype, m + h, e - m - h, q_view0, 0, q_views, vol, stream);
+    int rc = launch_packed<2>(p, Qp, q_dtype, b, m - b, q_view0, h, q_views, vol, stream, zr);
+    if (rc == IFDK_OK) rc = launch_packed<1>(p, Qp, q_dtype, m, b + h - m, q_view0, 0, q_views, vol, stream, zr);
+    if (rc == IFDK_OK) rc = launch_packed<1>(p, Qp, q_dtype, m + h, e - m - h, q_view0, 0, q_views, vol, stream, zr);
     return rc;
 }
 

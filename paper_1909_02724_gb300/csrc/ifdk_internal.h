@@ -148,11 +148,17 @@ void plan_packed(ifdk_plan_s *p);
 size_t packed_view_bytes(const ifdk_plan_s *p, int q_dtype);
 // Q: [n_views][nv][nu] -> Qp: [n_views][pk_rows][pk_nu][4].
 int launch_pack(ifdk_plan_s *p, const void *Q, int q_dtype, int n_views, void *Qp, cudaStream_t stream);
+// Mirror pairs [pair0, pair0 + pcount) of the volume, written to a column of
+// nz_out voxels (direct slab, then its mirror); pcount < 0: the whole volume.
+struct PkZRange {
+    int pair0 = 0, pcount = -1, nz_out = 0;
+};
 // Views [view_begin, view_begin + view_count) from packed views Qp that hold
 // views [q_view0, q_view0 + q_views): half-turn pairs inside the range (if
 // the plan pairs views) are back-projected together, the rest singly.
 int launch_backproject_packed(ifdk_plan_s *p, const void *Qp, int q_dtype, int view_begin, int view_count,
-                              int q_view0, int q_views, float *vol, cudaStream_t stream);
+                              int q_view0, int q_views, float *vol, cudaStream_t stream,
+                              const PkZRange &zr = PkZRange{});
 // Half-turn pairs (s, s + np/2) for s in [s_begin, s_begin + s_count); view s
 // is packed view s - q_view0 and its partner packed view s - q_view0 + q_pair_off.
 int launch_packed_pairs(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin, int s_count, int q_view0,

@@ -345,6 +345,25 @@ int ifdk_backproject_packed(ifdk_plan p, const void *Qp, int q_dtype, int view_b
     return launch_backproject_packed(p, Qp, q_dtype, view_begin, view_count, 0, p->g.np, vol, (cudaStream_t)stream);
 }
 
+int ifdk_backproject_packed_pairs(ifdk_plan p, const void *Qp, int q_dtype, int view_begin, int view_count,
+                                  int pair_begin, int pair_count, float *vol, void *stream)
+{
+    int rc = check_backproject_args(p, Qp, q_dtype, view_begin, view_count, vol);
+    if (rc != IFDK_OK) return rc;
+    if (!p->pk[q_dtype].path) return IFDK_ERR_UNSUPPORTED;
+    const int npairs = (p->g.nz + 1) / 2;
+    if (pair_begin < 0 || pair_count < 0 || pair_begin > npairs || pair_count > npairs - pair_begin)
+        return IFDK_ERR_INVALID;
+    if (view_count == 0 || pair_count == 0) return IFDK_OK;
+    PkZRange zr;
+    zr.pair0 = pair_begin;
+    zr.pcount = pair_count;
+    // the middle slice of an odd nz is its own mirror: stored once
+    zr.nz_out = 2 * pair_count - ((p->g.nz & 1) && pair_begin + pair_count == npairs ? 1 : 0);
+    return launch_backproject_packed(p, Qp, q_dtype, view_begin, view_count, 0, p->g.np, vol, (cudaStream_t)stream,
+                                     zr);
+}
+
 int ifdk_set_view_pairing(ifdk_plan p, int enable)
 {
     if (!p || (enable != 0 && enable != 1)) return IFDK_ERR_INVALID;

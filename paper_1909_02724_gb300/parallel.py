@@ -5,6 +5,9 @@ columns split the views (each column back-projects Np / C views into a
 partial volume, and the partial volumes are summed, the paper's MPI_Reduce),
 rows split the volume into z-slabs (each row back-projects every view into
 its own slab; slabs and their z-mirrors are independent, no collective).
+The paper's rows take sub-volumes in mirror pairs (a slab and its mirror
+slab), which keep Theorem 1 and so the packed back-projector: pair_shard,
+gather_pair_slabs.  slab_shard cuts plain contiguous slabs (off-centre plans).
 This module computes those partitions and the two collectives they need,
 through torch.distributed (NCCL for GPU tensors, gloo for CPU tensors).  The
 back-projection itself stays in the CUDA library: a view shard is a call with
@@ -105,6 +108,54 @@ def gather_slabs(slab_vol, full_vol=None, dst: int = 0, nz: int | None = None):
         for r in range(world):
             b, e = split_range(nz, world, r)
             full_vol[:, :, b:e] = parts[r][:, :, :e - b]
+    else:
+        dist.gather(send, dst=dst)
+    return full_vol
+
+
+def pair_shard(geom: Geometry, world: int, rank: int) -> tuple[int, int]:
+    """The mirror pairs a row worker reconstructs (the paper's sub-volumes: a z-slab
+    together with its mirror slab): (pair_begin, pair_count) over the (nz + 1) // 2
+    pairs (k, nz - 1 - k), for Plan.backproject_packed_pairs."""
+    b, e = split_range((geom.nz + 1) // 2, world, rank)
+    return b, e - b
+
+
+def place_pair_slab(full_vol, part, nz: int, pair_begin: int, pair_count: int):
+    """Writes a pair-range volume part [nx][ny][nz_out] (direct slab, then its
+    mirror) into its voxels of full_vol [nx][ny][nz]."""
+    if pair_count == 0:
+        return full_vol
+    nz_out = part.shape[2]
+    full_vol[:, :, pair_begin:pair_begin + pair_count] = part[:, :, :pair_count]
+    full_vol[:, :, nz - pair_begin - pair_count:nz - pair_begin] = part[:, :, nz_out - pair_count:]
+    return full_vol
+
+
+def gather_pair_slabs(part, full_vol, nz: int, dst: int = 0):
+    """Collects the pair-range volumes of a pair split (pair_shard) on rank dst
+    into full_vol [nx][ny][nz] (made here when None); padded to equal shape for
+    the gather.  Returns full_vol on dst."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        if full_vol is None:
+            full_vol = torch.empty(part.shape[:2] + (nz,), dtype=part.dtype, device=part.device)
+        return place_pair_slab(full_vol, part, nz, 0, (nz + 1) // 2)
+    world, rank = dist.get_world_size(), dist.get_rank()
+    npairs = (nz + 1) // 2
+    kmax = 2 * split_range(npairs, world, 0)[1]
+    send = torch.zeros(part.shape[:2] + (kmax,), dtype=part.dtype, device=part.device)
+    send[:, :, :part.shape[2]] = part
+    if rank == dst:
+        if full_vol is None:
+            full_vol = torch.empty(part.shape[:2] + (nz,), dtype=part.dtype, device=part.device)
+        parts = [torch.empty_like(send) for _ in range(world)]
+        dist.gather(send, gather_list=parts, dst=dst)
+        for r in range(world):
+            b, e = split_range(npairs, world, r)
+            depth = 2 * (e - b) - (1 if nz % 2 and e == npairs and e > b else 0)
+            place_pair_slab(full_vol, parts[r][:, :, :depth], nz, b, e - b)
     else:
         dist.gather(send, dst=dst)
     return full_vol

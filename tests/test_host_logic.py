@@ -176,7 +176,7 @@ def packed_zblocks(npairs, L):
     return npairs // L + -(-(npairs % L) // TAIL_L)
 
 
-def check_packed_windows(g, q_dtype, view_pairing=True, blocks=None):
+def check_packed_windows(g, q_dtype, view_pairing=True, blocks=None, pair0=0, pcount=None):
     info = B.ifdk_query_packed(g, q_dtype, view_pairing)
     if info["path"] == 0:
         return info
@@ -189,17 +189,21 @@ def check_packed_windows(g, q_dtype, view_pairing=True, blocks=None):
     ny_cols = g.ny // 2 if info["path"] == 2 else g.ny
     tiles_x, tiles_y = -(-g.nx // TILE), -(-ny_cols // TILE)
     npairs = (g.nz + 1) // 2
-    zblocks = packed_zblocks(npairs, L)
-    assert info["blocks"] == tiles_x * tiles_y * zblocks
+    if pcount is None:
+        zblocks = packed_zblocks(npairs, L)
+        assert info["blocks"] == tiles_x * tiles_y * zblocks
+        pcount = npairs
+    else:
+        zblocks = packed_zblocks(pcount, L)       # a pair-range launch
     if blocks is None:
         blocks = [(bx, by, bz) for bx in range(tiles_x) for by in range(tiles_y) for bz in range(zblocks)]
     tx, ty = np.meshgrid(np.arange(TILE), np.arange(TILE), indexing="ij")
     tx, ty = tx.ravel(), ty.ravel()
-    zfull = npairs // L
+    zfull = pcount // L
     for bx, by, bz in blocks:
-        # full z-blocks of L pairs, then tail blocks of TAIL_L pairs
+        # full z-blocks of L pairs, then tail blocks of TAIL_L pairs, from pair pair0 on
         Lb = L if bz < zfull else TAIL_L
-        k0 = bz * L if bz < zfull else zfull * L + (bz - zfull) * TAIL_L
+        k0 = pair0 + (bz * L if bz < zfull else zfull * L + (bz - zfull) * TAIL_L)
         p = np.arange(Lb)
         i0, j0 = bx * TILE, by * TILE
         kp0 = k0 - cz
@@ -229,7 +233,7 @@ def check_packed_windows(g, q_dtype, view_pairing=True, blocks=None):
         c_in = (cols >= -1) & (cols < -1 + info["row_elems"])
         c_off = (cols + 1 < 0) | (cols >= g.nu)          # both taps c, c + 1 off the detector
         assert np.all(c_in | c_off), (bx, by, bz)
-        written = (k0 + p) < npairs
+        written = (k0 + p) < pair0 + pcount
         rows = v0[:, None, None] + np.floor(vl[:, :, written])
         for rr in (rows, rows + 1):
             inside = (rr >= r0) & (rr < r0 + R)
@@ -353,3 +357,20 @@ def test_every_entry_point_refuses_a_null_plan_before_any_cuda_call():
             assert rc == B.IFDK_OK
         else:
             assert rc == B.IFDK_ERR_INVALID, (name, rc)
+
+
+def test_packed_windows_of_pair_ranges():
+    """Pair-range launches start their z-blocks at any pair: every tap of every
+    block still lies in its window."""
+    from tests.random_geometries import random_geometries
+    geoms = [g for _, g in random_geometries()] + [scaled_geometry(64, 64, 64), scaled_geometry(33, 48, 16, nz=33),
+                                                   circular(12, 64, 48, 1.5, 1.5, 36, 28, 22, 1.0, off_v=-4.5)]
+    rng = np.random.default_rng(8)
+    for g in geoms:
+        npairs = (g.nz + 1) // 2
+        for _ in range(3):
+            pb = int(rng.integers(0, npairs))
+            pc = int(rng.integers(1, npairs - pb + 1))
+            for dt in (B.IFDK_F32, B.IFDK_F16):
+                for pairing in (True, False):
+                    check_packed_windows(g, dt, pairing, pair0=pb, pcount=pc)

@@ -43,8 +43,8 @@ def _worker(rank, port, q):
         g, Q = _case()
         b, c = P.view_shard(g, WORLD, rank)
         out["views"] = (b, c)
-        part = torch.from_numpy(oracle.backproject(g, Q, b, c, threads=1))
-        P.reduce_volume(part, dst=0)
+        reduced = torch.from_numpy(oracle.backproject(g, Q, b, c, threads=1))
+        P.reduce_volume(reduced, dst=0)
 
         slab = P.slab_shard(g, WORLD, rank)
         out["slab"] = (slab.k_begin, slab.k_count)
@@ -52,9 +52,22 @@ def _worker(rank, port, q):
         full = torch.zeros((g.nx, g.ny, g.nz), dtype=torch.float64) if rank == 0 else None
         P.gather_slabs(vs, full, dst=0, nz=g.nz)
         made = P.gather_slabs(vs, None, dst=1, nz=g.nz)      # allocated on the destination rank
+        # the paper's sub-volumes: mirror pairs, direct slab then mirror slab
+        pb, pc = P.pair_shard(g.with_(vol_off_z=0.0), WORLD, rank)
+        gc = g.with_(vol_off_z=0.0)
+        ks = np.arange(pb, pb + pc)
+        depth = 2 * pc - (1 if g.nz % 2 and pb + pc == (g.nz + 1) // 2 else 0)
+        ii, jj = np.meshgrid(np.arange(g.nx), np.arange(g.ny), indexing="ij")
+        part = np.zeros((g.nx, g.ny, depth))
+        for t, k in enumerate(ks):
+            for kk, dst_k in ((k, t), (g.nz - 1 - k, depth - 1 - t)):
+                vox = np.stack([ii.ravel(), jj.ravel(), np.full(ii.size, kk)], 1)
+                part[:, :, dst_k] = oracle.backproject_voxels(gc, Q, vox, threads=1).reshape(g.nx, g.ny)
+        pairs_full = P.gather_pair_slabs(torch.from_numpy(part), None, g.nz, dst=0)
         if rank == 0:
-            out["reduced"] = part.numpy()
+            out["reduced"] = reduced.numpy()
             out["gathered"] = full.numpy()
+            out["pairs"] = pairs_full.numpy()
             assert made is None
         else:
             out["gathered_on_1"] = made.numpy()
@@ -153,3 +166,12 @@ def test_slab_split_gather_equals_single_process(results):
     # the slab's matrices differ from the volume's only in rounding (the Z shift)
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
     np.testing.assert_array_equal(results[1]["gathered_on_1"], got)
+
+
+def test_pair_split_gather_equals_single_process(results):
+    """Mirror-pair sub-volumes (pair_shard) of the centred volume, gathered."""
+    import oracle
+    g, Q = _case()
+    gc = g.with_(vol_off_z=0.0)
+    ref = oracle.backproject(gc, Q, threads=1)
+    np.testing.assert_allclose(results[0]["pairs"], ref, rtol=0, atol=1e-12 * np.abs(ref).max())
