@@ -1,14 +1,29 @@
 """Benchmark of the FDK hot path (filter + back-projection) on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload fdk512] [--dtype f32|f16|bf16]
+                    [--workload fdk2048] [--dtype f32|f16|bf16] [--batches 4]
 
-A step is one FDK reconstruction of the workload: ifdk_filter (cosine weight +
-Ram-Lak Toeplitz product) then ifdk_backproject (Algorithm 4) into a zeroed
-volume, inputs resident in HBM.  The metric is GUPS = Nx*Ny*Nz*Np / (T * 2^30)
-(Sec. 2.3 of the paper) over the whole step.  Under torchrun each rank
-reconstructs its own copy of the workload (independent problems: weak
-scaling, no collective on the data path); rank 0 prints one JSON line.
+The workload is fdk2048 (2048^3 from 2048 views of 2048 x 2048), the largest
+that fits one GPU.  A step is one batch of the paper's pipeline (Sec. 4:
+projections are filtered and back-projected in batches): ifdk_filter_views
+(cosine weight + Ram-Lak Toeplitz product on the tensor cores) on the batch's
+views, ifdk_pack_views, and ifdk_backproject_packed_batch (Algorithm 4, the
+batch's half-turn view pairs) into the accumulating volume; --batches steps
+make one reconstruction, whose first step zeroes the volume.  Inputs are
+resident in HBM.  The metric is GUPS = Nx*Ny*Nz*Np / (T * 2^30) (Sec. 2.3)
+over the timed steps (each step contributes Nx*Ny*Nz times its views).
+
+The same line carries: the back-projection kernel's roofline against the
+arithmetic rates measured on this GPU (ifdk_arith_rate); the other storage
+types (FP16 / BF16 filtered views, FP32 accumulation) as `storage_arms`,
+each one reconstruction on the same projections, with their error against
+the main arm's volume and the FP64 oracle; `e2e`, the same steps with each
+batch's projections copied in from pinned host memory and each finished
+volume copied out; and `cpu_baseline`, the oracle on the host cores (one
+thread and every core) with the accuracy of the timed volume on a sample of
+voxels.  Under torchrun each rank reconstructs its own copy of the workload
+(independent problems: weak scaling, no collective on the data path); rank 0
+prints one JSON line.
 
 --workload slab4096 (not a default line) times the streamed large-slab case:
 a step back-projects the 2048 FP16 filtered views, held in pinned host memory
@@ -16,8 +31,9 @@ a step back-projects the 2048 FP16 filtered views, held in pinned host memory
 zeroed slab, copying them to the device in 64-view chunks on a side stream
 while the back-projection runs; the copies are inside the timed region.
 
---impl reference times the FP64 CPU oracle (the reference arm: there is no reference code, only the paper) on
-the host cores, each step a bounded sample of the same workload.
+--impl reference times the FP64 CPU oracle (the reference arm: there is no
+reference code, only the paper) on the host cores, each step a bounded
+sample of the same workload.
 """
 from __future__ import annotations
 
@@ -45,7 +61,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fdk512")
+    ap.add_argument("--workload", default="fdk2048")
+    ap.add_argument("--batches", type=int, default=4,
+                    help="batches of half-turn view pairs per reconstruction (a step is one batch)")
+    ap.add_argument("--no-arms", action="store_true", help="skip the other storage types' arms")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
@@ -145,68 +164,179 @@ def profile_record(kernel_file: str, prof: str) -> dict:
         return {}
 
 
-def oracle_sample_fdk(w, E_rows_fn, n_slices: int, threads: int):
-    """Oracle FDK on n_slices z-slices centred on the mid-plane: filters the
-    detector rows those voxels touch and back-projects them.  Returns
-    (voxels, values, seconds, updates)."""
+def midplane_sample(g, n_vox: int, seed: int) -> np.ndarray:
+    """A seeded random subset of n_vox voxels of the two z-slices around the mid-plane."""
+    ks = np.array([max(0, g.nz // 2 - 1), g.nz // 2])
+    n_all = g.nx * g.ny * len(ks)
+    idx = np.random.default_rng(seed).choice(n_all, size=min(n_vox, n_all), replace=False)
+    kk, rest = np.divmod(idx, g.nx * g.ny)
+    ii, jj = np.divmod(rest, g.ny)
+    return np.stack([ii, jj, ks[kk]], 1).astype(np.int64)
+
+
+def midplane_rows(g):
+    """(view, row) indices of the detector rows that any voxel of the two mid-plane
+    z-slices can tap: per view, every row between the lowest and the highest row
+    the slices' corner columns tap (v - v_c is (B2 k' + B3) / z with z affine in
+    (i, j), so the columns' v lie between the corners'; Eq. 3, Theorems 2-3)."""
     import oracle
-    g = w.geom
-    k0 = g.nz // 2 - n_slices // 2
-    ks = np.arange(k0, k0 + n_slices)
-    ii, jj, kk = np.meshgrid(np.arange(g.nx), np.arange(g.ny), ks, indexing="ij")
-    vox = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], 1)
+    ks = sorted({max(0, g.nz // 2 - 1), g.nz // 2})
+    cor = np.array([[i, j, k] for i in (0, g.nx - 1) for j in (0, g.ny - 1) for k in ks], dtype=np.int64)
+    need = oracle.rows_needed(g, cor)
+    lo = need.argmax(1)
+    hi = g.nv - 1 - need[:, ::-1].argmax(1)
+    s_idx = np.concatenate([np.full(hi[s] - lo[s] + 1, s) for s in range(g.np) if need[s].any()])
+    r_idx = np.concatenate([np.arange(lo[s], hi[s] + 1) for s in range(g.np) if need[s].any()])
+    return s_idx.astype(np.int64), r_idx.astype(np.int64)
+
+
+def accuracy_sample(g) -> np.ndarray:
+    """Voxels on which the GPU volumes are compared with the oracle: the slices
+    k = 0, nz/2 - 1, nz/2, nz - 1 (the ends and the middle of the mirror pairs),
+    subsampled to at most 128 x 128 columns each."""
+    st = max(1, g.nx // 128)
+    ks = sorted({0, max(0, g.nz // 2 - 1), g.nz // 2, g.nz - 1})
+    ii, jj, kk = np.meshgrid(np.arange(0, g.nx, st), np.arange(0, g.ny, st), np.asarray(ks), indexing="ij")
+    return np.stack([ii.ravel(), jj.ravel(), kk.ravel()], 1).astype(np.int64)
+
+
+def oracle_rows(g, vox):
+    """(view index, row index) of every detector row the voxels' taps touch."""
+    import oracle
+    return np.nonzero(oracle.rows_needed(g, vox))
+
+
+def oracle_sample_fdk(g, E_rows, s_idx, r_idx, vox, threads: int):
+    """Oracle FDK at the voxels vox from the raw rows E_rows of (view s_idx, row
+    r_idx): Algorithm 1 on those rows, then Algorithm 2 at each voxel.  Returns
+    (values, seconds)."""
+    import oracle
     t0 = time.perf_counter()
-    need = oracle.rows_needed(g, vox)
-    s_idx, r_idx = np.nonzero(need)
-    E_rows = E_rows_fn(s_idx, r_idx)
-    Qs = oracle.filter_rows(g, E_rows, r_idx)
+    Qs = oracle.filter_rows(g, E_rows, r_idx, threads=threads)
     rowmap = -np.ones((g.np, g.nv), dtype=np.int64)
     rowmap[s_idx, r_idx] = np.arange(len(s_idx))
     vals = oracle.backproject_voxels(g, Qs, vox, rowmap=rowmap, threads=threads)
-    dt = time.perf_counter() - t0
-    return vox, vals, dt, vox.shape[0] * g.np
+    return vals, time.perf_counter() - t0
 
 
 def run_reference(args):
-    """The oracle on the host cores, each step a bounded sample of the workload."""
+    """The oracle on the host cores, each step a bounded sample of the workload:
+    Algorithm 1 on the detector rows that a seeded set of mid-plane voxels
+    touches, then Algorithm 2 at those voxels.  The rows' line integrals are
+    generated once, before the timed steps."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
-    from paper_1909_02724_gb300.phantom import chord_lengths, pixel_positions, source_positions, workload
+    from paper_1909_02724_gb300.phantom import line_integral_rows, workload
     w = workload(args.workload)
     g = w.geom
-    ell = w.phantom()
     threads = oracle.default_threads()
-
-    def rows_fn(s_idx, r_idx):   # exact FP64 line integrals of the needed rows only (no noise)
-        out = np.empty((len(s_idx), g.nu))
-        iu = np.arange(g.nu)
-        for s in np.unique(s_idx):
-            sel = np.nonzero(s_idx == s)[0]
-            beta = g.angles[s]
-            src = source_positions(g, [s])[0]
-            pix = pixel_positions(g, beta, iu[None, :], r_idx[sel][:, None])
-            out[sel] = chord_lengths(ell, src, pix)
-        return out
-
-    n_slices = 2
-    times, upd = [], 0
+    vox_all = midplane_sample(g, 1 << 20, 7)
+    s_idx, r_idx = midplane_rows(g)
+    E_rows = line_integral_rows(w.phantom(), g, s_idx, r_idx)   # exact FP64 line integrals, no noise
+    # size the sample for about 6 s per step from one calibration run
+    n = min(len(vox_all), 16384)
+    _, dt = oracle_sample_fdk(g, E_rows, s_idx, r_idx, vox_all[:n], threads)
+    n = int(min(len(vox_all), max(1024, n * 6.0 / max(dt, 1e-3))))
+    vox = vox_all[:n]
+    times = []
     for step in range(args.warmup + args.steps):
-        _, _, dt, u = oracle_sample_fdk(w, rows_fn, n_slices, threads)
+        _, dt = oracle_sample_fdk(g, E_rows, s_idx, r_idx, vox, threads)
         if step >= args.warmup:
             times.append(dt)
-            upd = u
+    upd = n * g.np
     value = upd / (float(np.mean(times)) * 2 ** 30)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_desc(w), "storage": "f64"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{n_slices} mid-plane z-slices ({upd} voxel-view updates) per step, "
-                                       "incl. generating and filtering the detector rows they touch"},
+                             "sample": f"{n} seeded voxels of the two mid-plane z-slices x {g.np} views "
+                                       f"({upd} voxel-view updates) per step, incl. filtering the "
+                                       f"{len(s_idx)} detector rows they touch"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def rel_l2_chunked(a, b) -> float:
+    """||a - b|| / ||b|| over two equal CUDA volumes, in FP64, slab by slab (no full temporary)."""
+    import torch
+    num = den = 0.0
+    step = max(1, a.shape[0] // 64)
+    for i in range(0, a.shape[0], step):
+        x, y = a[i:i + step].double(), b[i:i + step].double()
+        num += float(((x - y) ** 2).sum())
+        den += float((y ** 2).sum())
+        del x, y
+    return (num / den) ** 0.5 if den > 0 else float("nan")
+
+
+def sample_errors(vol, vox, ref) -> dict:
+    import torch
+    idx = [torch.from_numpy(vox[:, c]).to(vol.device) for c in range(3)]
+    v = vol[idx[0], idx[1], idx[2]].double().cpu().numpy()
+    return {"rel_l2": float(np.linalg.norm(v - ref) / np.linalg.norm(ref)),
+            "max_abs_over_max": float(np.max(np.abs(v - ref)) / np.max(np.abs(ref)))}
+
+
+def path_ceilings(rates: dict, n_sm: int, f_hz: float) -> dict:
+    """Arithmetic ceilings of the back-projection (GUPS) from the measured per-SM rates:
+    'alu10': the ten FP32 operations per update of Algorithms 3 and 4 (v, floor,
+    fraction, three lerps of sub + FMA, weighted accumulate) at the best measured
+    FP32 lane rate (FFMA or the packed FFMA2); per storage type, the minimal
+    instruction mix that storage's path needs per update, at the measured rates
+    (times of the different kinds added: they share the FMA issue):
+      f32:  the ten FP32 operations;
+      bf16: the ten FP32 operations + 2 integer ops widening the one new packed
+            row word pair per update (lop3 rate);
+      f16:  v, floor, fraction in FP32 (3), the three lerps in half2 (6 FP16
+            lanes) and the accumulate as one FP16-product FP32 FMA."""
+    r32 = max(rates["ffma"]["lane_ops_per_clk_sm"], rates["ffma2"]["lane_ops_per_clk_sm"])
+    rh = rates["hfma2"]["lane_ops_per_clk_sm"]
+    rm = rates["fma_f32_f16"]["lane_ops_per_clk_sm"]
+    ri = rates["lop3"]["lane_ops_per_clk_sm"]
+    per_clk = {"f32": 1.0 / (FP32_OPS_PER_UPDATE / r32),
+               "bf16": 1.0 / (FP32_OPS_PER_UPDATE / r32 + 2.0 / ri),
+               "f16": 1.0 / (3.0 / r32 + 6.0 / rh + 1.0 / rm)}
+    scale = n_sm * f_hz / 2 ** 30
+    return {"alu10": r32 / FP32_OPS_PER_UPDATE * scale, "fp32_lane_ops_per_clk_sm": r32,
+            **{k: v * scale for k, v in per_clk.items()},
+            "updates_per_clk_sm": per_clk}
+
+
+class Arm:
+    """One storage type's FDK in batches: the batch runner, its volume and its
+    back-projection events."""
+
+    def __init__(self, plan, batches, tdt, dev, standard):
+        from paper_1909_02724_gb300.api import BatchFdk
+        g = plan.geom
+        self.bf = BatchFdk(plan, batches, dtype=tdt, device=dev, packed=not standard)
+        self.vol = torch_empty_vol(g, dev)
+
+    def step(self, E, k, ev=None):
+        b = k % self.bf.batches
+        if b == 0:
+            self.vol.zero_()
+        self.bf.step(E, self.vol, b, ev_bp=ev)
+
+    def updates(self, k) -> int:
+        g = self.bf.plan.geom
+        return g.nx * g.ny * g.nz * 2 * self.bf.views(k % self.bf.batches)[1]
+
+    def finish(self, E, k_next):
+        """Runs the batches left in the current reconstruction (untimed), so that the
+        volume holds a whole reconstruction."""
+        k = k_next
+        while k % self.bf.batches != 0:
+            self.step(E, k)
+            k += 1
+
+
+def torch_empty_vol(g, dev):
+    import torch
+    return torch.empty((g.nx, g.ny, g.nz), dtype=torch.float32, device=dev)
 
 
 def run_ours(args):
@@ -218,9 +348,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     from paper_1909_02724_gb300 import binding as B
-    from paper_1909_02724_gb300.api import fdk_host, fdk_host_pipeline
+    from paper_1909_02724_gb300.api import batch_host_pipeline
     from paper_1909_02724_gb300.build import build
-    from paper_1909_02724_gb300.geometry import gups
     from paper_1909_02724_gb300.parallel import max_over_ranks
     from paper_1909_02724_gb300.phantom import workload, workload_projections_gpu
 
@@ -232,36 +361,25 @@ def run_ours(args):
     build()
     w = workload(args.workload)
     g = w.geom
-    tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.dtype]
+    dts = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+    tdt = dts[args.dtype]
+    dev = torch.device("cuda", local)
     plan = B.Plan(g)
     plan.set_view_pairing(not args.no_view_pairing)
     plan.set_view_split(args.view_split)
     packed = not args.standard and plan.has_packed(tdt)
-    splits = plan.view_split(tdt) if packed else 1
     info = plan.packed_info(tdt) if packed else plan.info(tdt)
-    dev = torch.device("cuda", local)
-    E = workload_projections_gpu(w)
-    Q = torch.empty((g.np, g.nv, g.nu), dtype=tdt, device=dev)
-    Qp = torch.empty(plan.packed_shape(tdt), dtype=tdt, device=dev) if packed else None
-    vol = torch.empty((g.nx, g.ny, g.nz), dtype=torch.float32, device=dev)
+    batches = max(1, min(args.batches, g.np // 2))
     stream = torch.cuda.current_stream()
+    E = workload_projections_gpu(w)
 
-    def step(ev_bp=None):
-        vol.zero_()
-        plan.filter(E, Q)
-        if packed:
-            plan.pack(Q, Qp)
-        if ev_bp is not None:
-            ev_bp[0].record(stream)
-        if packed:
-            plan.backproject_packed(Qp, vol)
-        else:
-            plan.backproject(Q, vol)
-        if ev_bp is not None:
-            ev_bp[1].record(stream)
+    # measured arithmetic rates of this GPU (the roofline's denominator)
+    rates = B.arith_rates(dev)
 
-    for _ in range(max(3, args.warmup)):
-        step()
+    arm = Arm(plan, batches, tdt, dev, args.standard)
+    for k in range(max(3, args.warmup)):
+        arm.step(E, k)
+    arm.finish(E, max(3, args.warmup))
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -275,78 +393,94 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0.record(stream)
     for k in range(args.steps):
-        step(bp_events[k])
+        arm.step(E, k, bp_events[k])
     t1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ck = clocks.stop()
+    arm.finish(E, args.steps)            # the volume holds one whole reconstruction
+    torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
-    bp_ms = float(np.mean([a.elapsed_time(b) for a, b in bp_events]))
+    upd_steps = sum(arm.updates(k) for k in range(args.steps))
+    bp_ms = [a.elapsed_time(b) for a, b in bp_events]
+    bp_gups = float(np.mean([arm.updates(k) / (t * 1e-3) / 2 ** 30 for k, t in enumerate(bp_ms)]))
     ms = max_over_ranks(ms, device=dev)
     ms_per_step = ms / args.steps
-    value = world * g.updates * args.steps / (ms * 1e-3) / 2 ** 30
+    value = world * upd_steps / (ms * 1e-3) / 2 ** 30
+
+    # launches of our kernels per step: per half of the batch the tensor-core filter (a
+    # split pre-pass and a GEMM per chunk of rows that fits the preferred workspace),
+    # then the pack (packed path) and the back-projection (one launch of half-turn
+    # pairs, else one per half), plus the sum of the partial volumes when a small
+    # volume splits its views
+    terms = 3 if tdt == torch.float32 else 2
+    ws_min, ws_pref = B.ifdk_filter_workspace_size(plan.handle, terms)
+    cap = ws_pref // (ws_min // 128)
+    half_rows = arm.bf.n * g.nv
+    bp_launches = 1 if (packed and info["path"] == 2) else 2
+    splits = plan.view_split(tdt) if packed else 1
+    per_step = 2 * 2 * -(-half_rows // cap) + (1 if packed else 0) + bp_launches * (2 if splits > 1 else 1)
+    launches = per_step * args.steps
 
     # output stage (Algorithm 4's reshape: k-fastest volume -> i-fastest slices), not part
-    # of the step; timed alone on the step's volume (512 MiB in, 512 MiB out: above L2)
+    # of the step; timed alone on the step's volume
     slices = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float32, device=dev)
     for _ in range(3):
-        plan.slices(vol, slices)
+        plan.slices(arm.vol, slices)
     sl_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
     for a, b in sl_events:
         a.record(stream)
-        plan.slices(vol, slices)
+        plan.slices(arm.vol, slices)
         b.record(stream)
     torch.cuda.synchronize()
     sl_ms = float(np.mean([a.elapsed_time(b) for a, b in sl_events]))
     sl_bytes = 8 * g.nx * g.ny * g.nz
     del slices
 
-    # launches of our kernels per step: tensor-core filter (a split pre-pass and a GEMM per
-    # chunk of rows that fits the preferred workspace), the pack (packed path) and one
-    # back-projection (the full scan pairs up, or is one range of single views), plus the
-    # sum of the partial volumes when a small volume splits its views
-    rows = g.np * g.nv
-    terms = 3 if tdt == torch.float32 else 2
-    ws_min, ws_pref = B.ifdk_filter_workspace_size(plan.handle, terms)
-    cap = ws_pref // (ws_min // 128)
-    launches = (2 * -(-rows // cap) + (2 if packed else 1) + (1 if splits > 1 else 0)) * args.steps
-
     # end to end through host buffers (pinned), copies inside the timed region: every
-    # step copies its projections in and its volume out; the copies of one step
-    # overlap the computation of its neighbours (two device buffers of each)
+    # step copies its batch of projections in; every finished reconstruction copies its
+    # volume out; the copies overlap the computation of the neighbouring steps
     e2e = None
     if not args.no_e2e:
         E_host = torch.empty(E.shape, dtype=torch.float32, pin_memory=True)
         E_host.copy_(E)
-        vol_host = torch.empty(vol.shape, dtype=torch.float32, pin_memory=True)
-        E2 = [E, torch.empty_like(E)]
-        vol2 = [vol, torch.empty_like(vol)]
-        e_steps = max(3, min(args.steps, 20))
-        fdk_host(plan, E_host, vol_host, E, Q, vol, Qp_dev=Qp)                  # one serial step (warm)
-        fdk_host_pipeline(plan, E_host, vol_host, E2, Q, vol2, Qp_dev=Qp, n_steps=2)
+        vol_host = torch.empty(arm.vol.shape, dtype=torch.float32, pin_memory=True)
+        E_b = [torch.empty((2 * arm.bf.n, g.nv, g.nu), dtype=torch.float32, device=dev) for _ in range(2)]
+        vol2 = [arm.vol, torch.empty_like(arm.vol)]
+        e_steps = max(batches, min(args.steps, 2 * batches))
+        batch_host_pipeline(arm.bf, E_host, vol_host, E_b, vol2, batches)          # warm
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         a = time.perf_counter()
-        fdk_host_pipeline(plan, E_host, vol_host, E2, Q, vol2, Qp_dev=Qp, n_steps=e_steps)
+        batch_host_pipeline(arm.bf, E_host, vol_host, E_b, vol2, e_steps)
         e_s = max_over_ranks(time.perf_counter() - a, device=dev)
-        e2e = {"value": world * g.updates * e_steps / e_s / 2 ** 30, "unit": UNIT,
-               "h2d_bytes_per_step": E.numel() * 4, "d2h_bytes_per_step": vol.numel() * 4,
-               "steps": e_steps, "overlap": "copies of step k overlap compute of steps k-1, k+1"}
-        del E2[1], vol2[1]
+        e_upd = sum(arm.updates(k) for k in range(e_steps))
+        h2d = sum(2 * arm.bf.views(k % batches)[1] for k in range(e_steps)) * g.nv * g.nu * 4
+        d2h = (e_steps // batches) * arm.vol.numel() * 4
+        e2e = {"value": world * e_upd / e_s / 2 ** 30, "unit": UNIT,
+               "h2d_bytes_per_step": h2d // e_steps, "d2h_bytes_per_step": d2h // e_steps,
+               "steps": e_steps,
+               "overlap": "batch copies in and volume copies out overlap the computation of neighbouring steps",
+               "d2h": "one volume per finished reconstruction (every %d steps), averaged per step" % batches}
+        del E_b, vol2, E_host, vol_host
+        arm.finish(E, 0)
+        arm.vol.zero_()
+        for k in range(batches):              # the timed volume again (the pipeline reused it)
+            arm.step(E, k)
+        torch.cuda.synchronize()
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    props = torch.cuda.get_device_properties(dev)
-    n_sm = props.multi_processor_count
+    n_sm = rates["n_sm"]
     peaks = measured_peaks()
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak_gups = n_sm * 128 * f_max / FP32_OPS_PER_UPDATE / 2 ** 30
-    achieved = gups(g, bp_ms * 1e-3)
+    ceil = path_ceilings(rates, n_sm, f_max)
+    nominal = n_sm * 128 * f_max / FP32_OPS_PER_UPDATE / 2 ** 30
     if packed:
         kname, kfile = "bp_packed_kernel", "ifdk_bp_packed.cu"
         prof = f"bp_packed_{args.workload}_{args.dtype}" + ("" if info["path"] == 2 else "_single")
@@ -354,15 +488,23 @@ def run_ours(args):
         kname = "bp_pairs_fold_kernel" if info["path"] == 1 else "bp_general_kernel"
         kfile, prof = "ifdk_bp.cu", f"bp_fold_{args.workload}"
     rec = profile_record(kfile, prof)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gups, "unit": UNIT,
-                "frac": achieved / peak_gups, "traffic": rec.get("dram_bytes_per_launch"),
-                "ncu": rec.get("ncu"),   # the binding counters of that capture (profiles/<prof>.md)
-                "kernel": kname,
-                "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz (MEASURED_PEAKS sm_max_mhz) "
-                              f"/ {FP32_OPS_PER_UPDATE} FP32 ops per update",
-                "frac_at_sampled_clock": (achieved / (peak_gups * ck["sm_mhz"] * 1e6 / f_max)
-                                          if ck.get("sm_mhz") else None),
-                "bp_ms_per_launch": bp_ms}
+
+    def roofline_of(gups_bp, dtype_key):
+        return {"bound": "alu", "achieved": gups_bp, "peak": ceil["alu10"], "unit": UNIT,
+                "frac": gups_bp / ceil["alu10"],
+                "peak_basis": f"{n_sm} SMs x {ceil['fp32_lane_ops_per_clk_sm']:.1f} FP32 lane ops per SM clock "
+                              f"(measured: best of FFMA / FFMA2, ifdk_arith_rate) x {f_max / 1e6:.0f} MHz "
+                              f"(MEASURED_PEAKS sm_max_mhz) / {FP32_OPS_PER_UPDATE} FP32 ops per update",
+                "peak_path": ceil[dtype_key], "frac_path": gups_bp / ceil[dtype_key],
+                "path_basis": f"minimal instruction mix of the {dtype_key} storage path at the measured rates",
+                "peak_nominal_128lane": nominal, "frac_nominal_128lane": gups_bp / nominal,
+                "frac_at_sampled_clock": (gups_bp / (ceil["alu10"] * ck["sm_mhz"] * 1e6 / f_max)
+                                          if ck.get("sm_mhz") else None)}
+
+    roofline = roofline_of(bp_gups, args.dtype)
+    roofline.update({"traffic": rec.get("dram_bytes_per_launch"), "ncu": rec.get("ncu"), "kernel": kname,
+                     "bp_ms_per_launch": float(np.mean(bp_ms)),
+                     "units_per_launch": arm.updates(0)})
 
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     output_stage = {"kernel": "slices_kernel<float>", "ms_per_launch": sl_ms,
@@ -371,25 +513,131 @@ def run_ours(args):
                     "frac": sl_bytes / (sl_ms * 1e-3) / 1e9 / hbm,
                     "peak_basis": "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
 
+    # oracle on a sample of voxels: the accuracy of every arm's volume
+    acc = None
+    if not args.no_cpu and world == 1:
+        acc = oracle_accuracy(w, E, accuracy_sample(g))
+
+    storage_arms = {}
+    if not args.no_arms and world == 1:
+        others = [d for d in ("f16", "bf16", "f32") if d != args.dtype]
+        vol_main = arm.vol
+        main_bf = arm.bf
+        del arm
+        for key in others:
+            main_bf.Q = main_bf.Qp = None      # the main arm's batch buffers are not needed any more
+            storage_arms[key] = run_arm(plan, batches, dts[key], dev, args.standard, E, vol_main, acc,
+                                        roofline_of, key)
+        torch.cuda.synchronize()
+        vol_for_acc = vol_main
+    else:
+        vol_for_acc = arm.vol
+
     cpu = None
     if not args.no_cpu and world == 1:
-        cpu = cpu_baseline(w, E, vol, plan, Q)
+        cpu = cpu_baseline(w, E)
+        cpu["accuracy_of_timed_volume"] = sample_errors(vol_for_acc, acc["vox"], acc["ref"])
+        cpu["accuracy_sample"] = acc["desc"]
+        cpu["oracle_seconds_for_accuracy_sample"] = acc["seconds"]
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": workload_desc(w), "storage": args.dtype, "accumulate": "f32",
+                       "step": f"one batch: filter + pack + back-project {2 * arm_views(plan, batches)} views "
+                               f"({arm_views(plan, batches)} half-turn pairs) of the {g.np}-view scan; "
+                               f"{batches} steps = one reconstruction (volume zeroed at its first)",
                        "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (E, Q, vol each >= 256 MiB)",
+                       "l2": "inputs larger than L2 (E, Q, Qp and the volume each >= 256 MiB)",
                        "bp_path": ("packed views" + (", half-turn view pairs" if info["path"] == 2 else ""))
                        if packed else "filtered views as stored",
                        "bp_launch": info, "view_split": splits},
             "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roofline,
-            "cpu_baseline": cpu, "output_stage": output_stage,
+            "storage_arms": storage_arms, "cpu_baseline": cpu, "output_stage": output_stage,
+            "arith_rates": {k: (v if k == "n_sm" else {"lane_ops_per_clk_sm": round(v["lane_ops_per_clk_sm"], 2),
+                                                        "warp_instr_per_clk_sm": round(v["warp_instr_per_clk_sm"], 3)})
+                            for k, v in rates.items()},
             "value_1e9": value * 2 ** 30 / 1e9}   # the same throughput in 10^9 updates/s
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def arm_views(plan, batches) -> int:
+    return -(-(plan.geom.np // 2) // batches)
+
+
+def run_arm(plan, batches, tdt, dev, standard, E, vol_ref, acc, roofline_of, key) -> dict:
+    """Another storage type on the same inputs: one warm-up batch, then one timed
+    reconstruction (every batch); its volume against the main arm's and the oracle."""
+    import torch
+    arm = Arm(plan, batches, tdt, dev, standard)
+    arm.step(E, 0)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(batches)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    t0.record(stream)
+    for k in range(batches):
+        arm.step(E, k, ev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    upd = sum(arm.updates(k) for k in range(batches))
+    bp = float(np.mean([arm.updates(k) / (a.elapsed_time(b) * 1e-3) / 2 ** 30 for k, (a, b) in enumerate(ev)]))
+    out = {"step_gups": upd / (t0.elapsed_time(t1) * 1e-3) / 2 ** 30, "bp_gups": bp,
+           "roofline": {k2: v for k2, v in roofline_of(bp, key).items()
+                        if k2 in ("frac", "peak_path", "frac_path", "frac_nominal_128lane")},
+           "rel_l2_vs_main_volume": rel_l2_chunked(arm.vol, vol_ref),
+           "split_terms": 3 if tdt == torch.float32 else 2}
+    if acc is not None:
+        out["vs_oracle_sample"] = sample_errors(arm.vol, acc["vox"], acc["ref"])
+    arm.bf.Q = arm.bf.Qp = None
+    del arm
+    torch.cuda.empty_cache()
+    return out
+
+
+def oracle_accuracy(w, E, vox) -> dict:
+    """Oracle values at the accuracy sample, from this run's projections E (the rows
+    the voxels touch, read back from the device in FP32 and widened)."""
+    import torch
+    import oracle
+    g = w.geom
+    s_idx, r_idx = oracle_rows(g, vox)
+    rows = []
+    for a in range(0, len(s_idx), 65536):
+        s = torch.from_numpy(s_idx[a:a + 65536]).to(E.device)
+        r = torch.from_numpy(r_idx[a:a + 65536]).to(E.device)
+        rows.append(E[s, r].double().cpu().numpy())
+    ref, dt = oracle_sample_fdk(g, np.concatenate(rows), s_idx, r_idx, vox, oracle.default_threads())
+    ks = sorted(set(int(k) for k in vox[:, 2]))
+    return {"vox": vox, "ref": ref, "seconds": dt,
+            "desc": f"{len(vox)} voxels: z-slices {ks}, every {max(1, g.nx // 128)}th column in i and j"}
+
+
+def cpu_baseline(w, E) -> dict:
+    """The oracle on the host cores on a bounded sample (seeded mid-plane voxels, all
+    views), with one thread and with every core, about 10 s each."""
+    import torch
+    import oracle
+    g = w.geom
+    cores = oracle.default_threads()
+    vox_all = midplane_sample(g, 1 << 20, 7)
+    s_idx, r_idx = midplane_rows(g)
+    E_rows = E[torch.from_numpy(s_idx).to(E.device), torch.from_numpy(r_idx).to(E.device)].double().cpu().numpy()
+    out = {"unit": UNIT, "kind": "oracle"}
+    for label, threads in (("all_cores", cores), ("one_thread", 1)):
+        n = min(len(vox_all), 4096 * threads)
+        _, dt = oracle_sample_fdk(g, E_rows, s_idx, r_idx, vox_all[:n], threads)
+        n = int(min(len(vox_all), max(256, n * 10.0 / max(dt, 1e-3))))
+        _, dt = oracle_sample_fdk(g, E_rows, s_idx, r_idx, vox_all[:n], threads)
+        out[label] = {"value": n * g.np / dt / 2 ** 30, "threads": threads, "voxels": n, "seconds": dt}
+    out["value"] = out["all_cores"]["value"]
+    out["cores"] = cores
+    out["sample"] = (f"seeded voxels of the two mid-plane z-slices x all {g.np} views (all_cores: "
+                     f"{out['all_cores']['voxels']}, one_thread: {out['one_thread']['voxels']} voxels), incl. "
+                     f"filtering the detector rows they touch (FP64 C, pthreads)")
+    return out
 
 
 def run_slab(args):
@@ -492,37 +740,6 @@ def run_slab(args):
                          "kernel": "bp_packed_kernel" if packed else "bp_pairs_fold_kernel"},
             "cpu_baseline": None}
     print(json.dumps(line), flush=True)
-
-
-def cpu_baseline(w, E, vol_gpu_unused, plan, Q):
-    """The oracle on the host cores on a bounded sample (mid-plane slab), plus the
-    accuracy of this run's GPU volume on the same voxels."""
-    import torch
-    import oracle
-    g = w.geom
-    threads = oracle.default_threads()
-    E_cpu = None
-
-    def rows_fn(s_idx, r_idx):
-        nonlocal E_cpu
-        return E[torch.from_numpy(s_idx).to(E.device), torch.from_numpy(r_idx).to(E.device)].double().cpu().numpy()
-
-    # calibrate on one slice, then size the sample to about 12 s
-    _, _, dt1, _ = oracle_sample_fdk(w, rows_fn, 1, threads)
-    n_slices = int(max(1, min(g.nz, round(12.0 / max(dt1, 1e-3)))))
-    vox, vals, dt, upd = oracle_sample_fdk(w, rows_fn, n_slices, threads)
-    # GPU FDK of the same inputs (FP32 storage, as timed), compared on the sample
-    vol = torch.zeros((g.nx, g.ny, g.nz), dtype=torch.float32, device=E.device)
-    Qf = torch.empty(E.shape, dtype=torch.float32, device=E.device)
-    plan.filter(E, Qf)
-    plan.backproject(Qf, vol)
-    v = vol.cpu().numpy()[vox[:, 0], vox[:, 1], vox[:, 2]].astype(np.float64)
-    rel = float(np.linalg.norm(v - vals) / np.linalg.norm(vals))
-    mx = float(np.max(np.abs(v - vals)) / np.max(np.abs(vals)))
-    return {"value": upd / dt / 2 ** 30, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n_slices} mid-plane z-slices of {g.nx}x{g.ny} ({upd} voxel-view updates), "
-                      "incl. filtering the detector rows they touch (FP64 C, pthreads)",
-            "seconds": dt, "gpu_f32_vs_oracle_on_sample": {"rel_l2": rel, "max_abs_over_max": mx}}
 
 
 def main():

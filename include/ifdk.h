@@ -136,6 +136,17 @@ int ifdk_filter(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_ter
 int ifdk_filter_max(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms,
                     void *workspace, size_t workspace_bytes, float *view_max, void *stream);
 
+/* ifdk_filter on a range of views: Ev (device FP32 [view_count][nv][nu]) holds
+   views [view_begin, view_begin + view_count) and Qv (device [view_count][nv][nu]
+   of q_dtype) receives them filtered, the same values ifdk_filter gives those
+   views (row by row the same arithmetic).  This is the filtering of one batch
+   of the paper's pipeline (Sec. 4: projections are filtered in batches as they
+   arrive and handed on to the back-projection).  Arguments, workspace,
+   alignment and errors as ifdk_filter; a range outside [0, np) returns
+   IFDK_ERR_INVALID, view_count = 0 does nothing. */
+int ifdk_filter_views(ifdk_plan p, const float *Ev, void *Qv, int q_dtype, int split_terms, int view_begin,
+                      int view_count, void *workspace, size_t workspace_bytes, void *stream);
+
 /* Workspace of ifdk_filter for split_terms: the minimum (one 128-row tile of
    split operands) and a preferred size (every row in one launch, up to 1 GiB).
    Either pointer may be NULL.  0 bytes for split_terms = 0. */
@@ -262,6 +273,20 @@ int ifdk_set_view_pairing(ifdk_plan p, int enable);
    range outside [0, (nz+1)/2). */
 int ifdk_backproject_packed_pairs(ifdk_plan p, const void *Qp, int q_dtype, int view_begin, int view_count,
                                   int pair_begin, int pair_count, float *vol, void *stream);
+
+/* Back-projection of one batch of half-turn view pairs (the paper's pipeline
+   back-projects views in batches as they are filtered, Sec. 4): Qpb holds
+   2 view_count packed views (ifdk_pack_views layout), first views
+   [view_begin, view_begin + view_count), then their partners [view_begin +
+   np/2, view_begin + np/2 + view_count); all of them are added into vol
+   (device FP32 [nx][ny][nz], ACCUMULATED into).  With half-turn view pairing
+   on and available the pairs are back-projected together (one launch),
+   otherwise singly; either way the arithmetic per voxel is that of
+   ifdk_backproject_packed over the same views.  np must be even and
+   view_begin + view_count <= np/2 (else IFDK_ERR_INVALID).  Alignment and
+   other errors as ifdk_backproject_packed. */
+int ifdk_backproject_packed_batch(ifdk_plan p, const void *Qpb, int q_dtype, int view_begin, int view_count,
+                                  float *vol, void *stream);
 
 /* Describes a full-range ifdk_backproject_packed launch with q_dtype:
    info[0] = path (2 = half-turn view pairs, 1 = single views, 0 = packed
@@ -407,6 +432,30 @@ int ifdk_query_backproject(const ifdk_geometry *g, int q_dtype, int64_t info[10]
    so that v_c moves by -*row_begin) back-projects the same volume. */
 int ifdk_query_rows(const ifdk_geometry *g, int view_begin, int view_count, int *row_begin,
                     int *row_count);
+
+/* Arithmetic rate probe: the denominator of the back-projection's roofline.
+   Algorithm 4 with Algorithm 3 costs about ten arithmetic operations per
+   voxel-view update (GUPS, Sec. 2.3) and very few projection bytes, so its
+   bound is an arithmetic issue rate.  This call launches `blocks` blocks of
+   1024 threads (one per SM: pass the SM count), each thread running 8
+   independent chains of `iters` * 16 instructions of one kind:
+     IFDK_RATE_FFMA        fma.rn.f32        (1 FP32 lane operation)
+     IFDK_RATE_FFMA2       fma.rn.f32x2      (2: packed FP32 pair)
+     IFDK_RATE_HFMA2       fma.rn.f16x2      (2: packed FP16 pair)
+     IFDK_RATE_FMA_F32_F16 fma.rn.f32.f16    (1: FP16 product, FP32 sum)
+     IFDK_RATE_LOP3        lop3.b32          (1: integer logic)
+   Each block records its SM clock (clock64) before and after its loop and its
+   SM id: clocks[3 b + 0..2] = start, end, smid (device int64 [3 * blocks],
+   8-byte aligned).  sink: device FP32 [blocks * 1024], overwritten with the
+   chains' results.  out[0] = instructions per thread, out[1] = lane
+   operations per instruction (host).  Rate per SM = 1024 * out[0] * out[1]
+   / (end - start), lane operations per SM clock; the loop's own counter
+   instructions (under 3 %) make it a lower bound.  Asynchronous on `stream`.
+   The paper has no counterpart. */
+enum { IFDK_RATE_FFMA = 0, IFDK_RATE_FFMA2 = 1, IFDK_RATE_HFMA2 = 2, IFDK_RATE_FMA_F32_F16 = 3,
+       IFDK_RATE_LOP3 = 4 };
+int ifdk_arith_rate(int kind, int blocks, long long iters, float *sink, long long *clocks,
+                    int64_t out[2], void *stream);
 
 /* Human-readable text for a status code (static storage). */
 const char *ifdk_status_string(int code);

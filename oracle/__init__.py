@@ -182,13 +182,14 @@ def short_scan_weights(geom) -> np.ndarray:
 
 
 def filter_rows(geom, E_rows: np.ndarray, rows_v: np.ndarray, method: str = "auto",
-                rows_s: np.ndarray | None = None) -> np.ndarray:
+                rows_s: np.ndarray | None = None, threads: int | None = None) -> np.ndarray:
     """Algorithm 1 on selected rows: Q = F_ramp (x) (E . F_cos).
 
     E_rows: (R, nu) raw projection rows; rows_v: (R,) detector row index of each
     (selects the F_cos row).  method: 'direct', 'fft' or 'auto' (fft for nu >= 256).
     rows_s: (R,) view index of each row, needed for a short-scan geometry (its rows
-    are weighted by short_scan_weights before the filter).
+    are weighted by short_scan_weights before the filter).  threads: host threads
+    over rows (default: every core).
     """
     lib, g = _load(), _GeomHolder(geom)
     E_rows = np.ascontiguousarray(E_rows, dtype=np.float64).reshape(-1, geom.nu)
@@ -202,7 +203,7 @@ def filter_rows(geom, E_rows: np.ndarray, rows_v: np.ndarray, method: str = "aut
         method = "fft" if geom.nu >= 256 else "direct"
     fn = lib.orc_filter_rows_fft if method == "fft" else lib.orc_filter_rows_direct
     n = E_rows.shape[0]
-    nth = min(default_threads(), max(1, n // 64))
+    nth = min(threads or default_threads(), max(1, n // 64))
     if nth <= 1:
         fn(g.ref, _ptr(E_rows), _ptr(rows_v, ctypes.c_int), n, _ptr(Q))
         return Q

@@ -2,7 +2,9 @@
 
 ``fdk`` reconstructs on the device; ``fdk_host`` is the same call on host
 buffers: it copies the projections in (from pinned memory), filters,
-back-projects and copies the volume out, all on one stream.  When the plan
+back-projects and copies the volume out, all on one stream.  ``BatchFdk``
+reconstructs in batches of half-turn view pairs and ``batch_host_pipeline``
+streams those batches from host memory.  When the plan
 has packed views (centred volume, 2 v_c integral) and a packed buffer is
 given or allowed, the filtered views are packed (ifdk_pack_views) and
 back-projected by the packed kernel; otherwise by ifdk_backproject.  Every
@@ -101,6 +103,122 @@ def fdk_host_pipeline(plan: Plan, E_host: torch.Tensor, vol_host: torch.Tensor, 
             s_out.wait_event(computed[b])
             vol_host.copy_(vol_dev[b], non_blocking=True)
             drained[b].record(s_out)
+    s_out.synchronize()
+    s_c.synchronize()
+    return vol_host
+
+
+class BatchFdk:
+    """FDK of a scan in batches of half-turn view pairs, the way the paper's
+    pipeline (Sec. 4) filters and back-projects projections in batches as they
+    arrive: batch b holds views [b n, b n + n) and their partners
+    [np/2 + b n, np/2 + b n + n), n = np / (2 batches) (the last batch takes the
+    remainder).  One batch is ifdk_filter_views on each half,
+    ifdk_pack_views on the 2 n filtered views and
+    ifdk_backproject_packed_batch into the accumulating volume (or, without
+    packed views, ifdk_backproject_views on each half).  The batch buffers
+    (filtered and packed views of one batch) are made here, once."""
+
+    def __init__(self, plan: Plan, batches: int, dtype=torch.float32, split_terms: int | None = None,
+                 device=None, packed: bool = True):
+        g = plan.geom
+        if g.np % 2 != 0 or not 1 <= batches <= g.np // 2:
+            raise ValueError("batches of half-turn pairs need an even view count and 1 <= batches <= np / 2")
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.plan, self.batches, self.dtype, self.split_terms = plan, batches, dtype, split_terms
+        self.half = g.np // 2
+        self.n = -(-self.half // batches)
+        self.packed = packed and plan.has_packed(dtype)
+        self.Q = torch.empty((2 * self.n, g.nv, g.nu), dtype=dtype, device=dev)
+        self.Qp = (torch.empty((2 * self.n,) + plan.packed_shape(dtype)[1:], dtype=dtype, device=dev)
+                   if self.packed else None)
+
+    def views(self, b: int) -> tuple[int, int]:
+        """(first view, view count) of the first half of batch b; the second half is
+        the same range shifted by np / 2."""
+        s0 = b * self.n
+        return s0, max(0, min(self.n, self.half - s0))
+
+    def step(self, E: torch.Tensor, vol: torch.Tensor, b: int, stream=None, ev_bp=None) -> None:
+        """Batch b of the scan E (float32 CUDA [np][nv][nu], or a buffer holding just this
+        batch: its n views, then their n partners, n = views(b)[1]) added into vol.  ev_bp: optional
+        (start, end) CUDA events recorded around the back-projection launch."""
+        g = self.plan.geom
+        s0, n = self.views(b)
+        if n == 0:
+            return
+        if E.shape[0] == g.np:
+            Ea, Eb = E[s0:s0 + n], E[self.half + s0:self.half + s0 + n]
+        else:
+            Ea, Eb = E[:n], E[n:2 * n]
+        Qa, Qb = self.Q[:n], self.Q[n:2 * n]
+        self.plan.filter_views(Ea, Qa, view_begin=s0, split_terms=self.split_terms, stream=stream)
+        self.plan.filter_views(Eb, Qb, view_begin=self.half + s0, split_terms=self.split_terms, stream=stream)
+        s = torch.cuda.current_stream() if stream is None else stream
+        if self.packed:
+            Qpb = self.Qp[:2 * n]
+            self.plan.pack(self.Q[:2 * n], Qpb, stream=stream)
+            if ev_bp is not None:
+                ev_bp[0].record(s)
+            self.plan.backproject_packed_batch(Qpb, s0, n, vol, stream=stream)
+        else:
+            if ev_bp is not None:
+                ev_bp[0].record(s)
+            self.plan.backproject_views(Qa, vol, view_begin=s0, stream=stream)
+            self.plan.backproject_views(Qb, vol, view_begin=self.half + s0, stream=stream)
+        if ev_bp is not None:
+            ev_bp[1].record(s)
+
+    def reconstruct(self, E: torch.Tensor, vol: torch.Tensor, stream=None) -> torch.Tensor:
+        """vol (+)= FDK of the whole scan E, batch by batch."""
+        for b in range(self.batches):
+            self.step(E, vol, b, stream=stream)
+        return vol
+
+
+def batch_host_pipeline(bf: BatchFdk, E_host: torch.Tensor, vol_host: torch.Tensor, E_dev: list, vol_dev: list,
+                        n_steps: int) -> torch.Tensor:
+    """n_steps batches (cycling over the scan's batches; every `batches` steps one
+    reconstruction) from host projections E_host (pinned float32 [np][nv][nu]) to a
+    host volume vol_host: each step copies its batch's views in (E_dev: two device
+    buffers of [2 n][nv][nu], double-buffered), and each finished reconstruction
+    copies its volume out (vol_dev: two device volumes).  Three streams (in,
+    compute, out) ordered by events, so the copies of one step overlap the
+    computation of its neighbours.  Returns once the last volume that finished
+    is in vol_host (a reconstruction left unfinished stays on the device)."""
+    g = bf.plan.geom
+    dev = E_dev[0].device
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    s_c = torch.cuda.current_stream(dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    used = [torch.cuda.Event() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+    drained = [torch.cuda.Event() for _ in range(2)]
+    n_rec = [0, 0]
+    for k in range(n_steps):
+        e, b = k & 1, k % bf.batches
+        r = (k // bf.batches) & 1                          # volume buffer of this reconstruction
+        s0, n = bf.views(b)
+        with torch.cuda.stream(s_in):
+            if k >= 2:
+                s_in.wait_event(used[e])                   # step k-2's filters have read E_dev[e]
+            E_dev[e][:n].copy_(E_host[s0:s0 + n], non_blocking=True)
+            E_dev[e][n:2 * n].copy_(E_host[bf.half + s0:bf.half + s0 + n], non_blocking=True)
+            copied[e].record(s_in)
+        s_c.wait_event(copied[e])
+        if b == 0:
+            if n_rec[r] > 0:
+                s_c.wait_event(drained[r])                 # the volume two reconstructions back has left
+            vol_dev[r].zero_()
+        bf.step(E_dev[e], vol_dev[r], b, stream=s_c)
+        used[e].record(s_c)
+        if b == bf.batches - 1:
+            done[r].record(s_c)
+            n_rec[r] += 1
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(done[r])
+                vol_host.copy_(vol_dev[r], non_blocking=True)
+                drained[r].record(s_out)
     s_out.synchronize()
     s_c.synchronize()
     return vol_host

@@ -34,7 +34,8 @@ EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_
            "ifdk_packed_size", "ifdk_pack_views", "ifdk_backproject_packed", "ifdk_set_view_pairing",
            "ifdk_backproject_packed_info", "ifdk_query_packed", "ifdk_volume_slices",
            "ifdk_set_view_split", "ifdk_view_split", "ifdk_filter_max", "ifdk_set_short_scan",
-           "ifdk_backproject_packed_pairs")
+           "ifdk_backproject_packed_pairs", "ifdk_filter_views", "ifdk_backproject_packed_batch",
+           "ifdk_arith_rate")
 
 
 class IfdkError(RuntimeError):
@@ -103,6 +104,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.ifdk_set_short_scan.argtypes = [vp, i32]
         lib.ifdk_backproject_packed_pairs.argtypes = [vp, vp, i32, i32, i32, i32, i32, vp, vp]
         lib.ifdk_view_split.argtypes = [vp, i32, ctypes.POINTER(i32)]
+        lib.ifdk_filter_views.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp, ctypes.c_size_t, vp]
+        lib.ifdk_backproject_packed_batch.argtypes = [vp, vp, i32, i32, i32, vp, vp]
+        lib.ifdk_arith_rate.argtypes = [i32, i32, ctypes.c_longlong, vp, vp, ctypes.POINTER(i64), vp]
         lib.ifdk_status_string.argtypes = [i32]
         lib.ifdk_status_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -257,6 +261,30 @@ def ifdk_backproject_packed_pairs(plan: int, Qp, q_dtype: int, view_begin: int, 
                                                         int(view_count), int(pair_begin), int(pair_count),
                                                         _addr(vol), _stream(stream)),
            "ifdk_backproject_packed_pairs")
+
+
+def ifdk_filter_views(plan: int, Ev, Qv, q_dtype: int, split_terms: int, view_begin: int, view_count: int,
+                      workspace=None, workspace_bytes: int = 0, stream=None) -> None:
+    """Ev, Qv hold only views [view_begin, view_begin + view_count)."""
+    _check(load_library().ifdk_filter_views(plan, _addr(Ev), _addr(Qv), int(q_dtype), int(split_terms),
+                                            int(view_begin), int(view_count), _addr(workspace),
+                                            int(workspace_bytes), _stream(stream)), "ifdk_filter_views")
+
+
+def ifdk_backproject_packed_batch(plan: int, Qpb, q_dtype: int, view_begin: int, view_count: int, vol,
+                                  stream=None) -> None:
+    """Qpb: packed views [view_begin, +view_count) then their half-turn partners."""
+    _check(load_library().ifdk_backproject_packed_batch(plan, _addr(Qpb), int(q_dtype), int(view_begin),
+                                                        int(view_count), _addr(vol), _stream(stream)),
+           "ifdk_backproject_packed_batch")
+
+
+def ifdk_arith_rate(kind: int, blocks: int, iters: int, sink, clocks, stream=None) -> tuple[int, int]:
+    """Launches the arithmetic rate probe; returns (instructions per thread, lanes per instruction)."""
+    out = (ctypes.c_int64 * 2)()
+    _check(load_library().ifdk_arith_rate(int(kind), int(blocks), int(iters), _addr(sink), _addr(clocks), out,
+                                          _stream(stream)), "ifdk_arith_rate")
+    return int(out[0]), int(out[1])
 
 
 def pair_slab_depth(nz: int, pair_begin: int, pair_count: int) -> int:
@@ -420,6 +448,26 @@ class Plan:
             ifdk_filter_max(self.handle, E, Q, dtype_code(Q.dtype), split_terms, ws, ws_bytes, view_max, stream)
         return Q
 
+    def filter_views(self, Ev, Qv=None, view_begin: int = 0, dtype=None, split_terms: int | None = None,
+                     stream=None):
+        """ifdk_filter_views: Ev (views, nv, nu) FP32 holds views [view_begin, view_begin + len(Ev));
+        Qv receives them filtered (split_terms as in filter)."""
+        import torch
+        g = self.geom
+        if (not Ev.is_cuda or not Ev.is_contiguous() or Ev.dim() != 3 or tuple(Ev.shape[1:]) != (g.nv, g.nu)
+                or Ev.dtype != torch.float32):
+            raise ValueError(f"Ev must be a contiguous float32 CUDA tensor of shape (views, {g.nv}, {g.nu})")
+        if Qv is None:
+            Qv = torch.empty_like(Ev, dtype=dtype or torch.float32)
+        if not Qv.is_cuda or not Qv.is_contiguous() or tuple(Qv.shape) != tuple(Ev.shape):
+            raise ValueError(f"Qv must be a contiguous CUDA tensor of shape {tuple(Ev.shape)}")
+        if split_terms is None:
+            split_terms = 3 if Qv.dtype == torch.float32 else 2
+        ws, ws_bytes = self.workspace(split_terms, Ev.device)
+        ifdk_filter_views(self.handle, Ev, Qv, dtype_code(Qv.dtype), split_terms, view_begin, Ev.shape[0], ws,
+                          ws_bytes, stream)
+        return Qv
+
     def filter_adjoint(self, G_Q, out=None, stream=None):
         import torch
         self._check_views(G_Q, "G_Q")
@@ -538,6 +586,20 @@ class Plan:
                                       vol, stream)
         return vol
 
+    def backproject_packed_batch(self, Qpb, view_begin: int, view_count: int, vol=None, stream=None):
+        """ifdk_backproject_packed_batch: Qpb (2 view_count, rows, row_elems, 4) holds the packed
+        views [view_begin, +view_count) then their partners [view_begin + np/2, ...)."""
+        import torch
+        g = self.geom
+        shape = (2 * view_count,) + self.packed_shape(Qpb.dtype)[1:]
+        if not Qpb.is_cuda or not Qpb.is_contiguous() or tuple(Qpb.shape) != shape:
+            raise ValueError(f"Qpb must be a contiguous CUDA tensor of shape {shape}")
+        if vol is None:
+            vol = torch.zeros((g.nx, g.ny, g.nz), dtype=torch.float32, device=Qpb.device)
+        self._check_vol(vol)
+        ifdk_backproject_packed_batch(self.handle, Qpb, dtype_code(Qpb.dtype), view_begin, view_count, vol, stream)
+        return vol
+
     def set_view_pairing(self, enable: bool) -> None:
         """Half-turn view pairing of the packed back-projection (on by default)."""
         ifdk_set_view_pairing(self.handle, enable)
@@ -589,3 +651,34 @@ class Plan:
         import torch
         code = dtype if isinstance(dtype, int) else dtype_code(dtype if dtype is not None else torch.float32)
         return ifdk_backproject_info(self.handle, code)
+
+
+IFDK_RATE_FFMA, IFDK_RATE_FFMA2, IFDK_RATE_HFMA2, IFDK_RATE_FMA_F32_F16, IFDK_RATE_LOP3 = 0, 1, 2, 3, 4
+RATE_KINDS = {"ffma": IFDK_RATE_FFMA, "ffma2": IFDK_RATE_FFMA2, "hfma2": IFDK_RATE_HFMA2,
+              "fma_f32_f16": IFDK_RATE_FMA_F32_F16, "lop3": IFDK_RATE_LOP3}
+
+
+def arith_rates(device=None, iters: int = 2048, kinds=tuple(RATE_KINDS)) -> dict:
+    """Per-SM arithmetic rates of the GPU (ifdk_arith_rate): for each kind,
+    lane operations and warp instructions per SM clock (median over blocks,
+    each block timed by its own SM clock), with the SM count."""
+    import numpy as np
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(n_sm * 1024, dtype=torch.float32, device=dev)
+    clk = torch.empty(3 * n_sm, dtype=torch.int64, device=dev)
+    out = {"n_sm": n_sm}
+    for name in kinds:
+        ifdk_arith_rate(RATE_KINDS[name], n_sm, 64, sink, clk)          # warm
+        per_thread, lanes = ifdk_arith_rate(RATE_KINDS[name], n_sm, iters, sink, clk)
+        torch.cuda.synchronize(dev)
+        c = clk.view(n_sm, 3).cpu().numpy()
+        cyc = (c[:, 1] - c[:, 0]).astype(np.float64)
+        lane_ops = 1024.0 * per_thread * lanes
+        rates = lane_ops / cyc
+        out[name] = {"lane_ops_per_clk_sm": float(np.median(rates)), "lanes_per_instr": lanes,
+                     "warp_instr_per_clk_sm": float(np.median(rates)) / (32 * lanes),
+                     "min": float(rates.min()), "max": float(rates.max()),
+                     "sms_seen": int(len(np.unique(c[:, 2])))}
+    return out

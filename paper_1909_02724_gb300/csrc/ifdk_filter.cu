@@ -146,11 +146,13 @@ __global__ void __launch_bounds__(kFThreads)
     }
 }
 
+// E, Q: views [view_begin, view_begin + view_count) (row 0 = row 0 of view view_begin)
 template <typename TQ, bool ADJ>
-int launch_simt(ifdk_plan_s *p, const float *E, void *Q, cudaStream_t stream, unsigned int *view_max = nullptr)
+int launch_simt(ifdk_plan_s *p, const float *E, void *Q, cudaStream_t stream, unsigned int *view_max, int view_begin,
+                int view_count)
 {
     const ifdk_geometry &g = p->g;
-    const long long rows = (long long)g.np * g.nv;
+    const long long rows = (long long)view_count * g.nv;
     const int len = ADJ ? g.nu : g.nu + 1;
     const size_t smem = sizeof(float) * ((size_t)kRows * len + kOutPerBlock + len + 4);
     if (smem > 220 * 1024) return IFDK_ERR_UNSUPPORTED;
@@ -167,7 +169,7 @@ int launch_simt(ifdk_plan_s *p, const float *E, void *Q, cudaStream_t stream, un
         const long long nr = rows - r0 < chunk ? rows - r0 : chunk;
         kern<<<dim3(gx, (unsigned)((nr + kRows - 1) / kRows)), kFThreads, smem, stream>>>(
             E + r0 * g.nu, static_cast<TQ *>(Q) + r0 * g.nu, p->d_fcos, p->d_fcos_lo, ADJ ? p->d_taps : p->d_gsum,
-            g.nu, g.nv, nr, view_max, (int)(r0 / g.nv), p->d_sweight);
+            g.nu, g.nv, nr, view_max, view_begin + (int)(r0 / g.nv), p->d_sweight);
         if (cudaGetLastError() != cudaSuccess) return IFDK_ERR_CUDA;
     }
     return IFDK_OK;
@@ -176,16 +178,19 @@ int launch_simt(ifdk_plan_s *p, const float *E, void *Q, cudaStream_t stream, un
 }  // namespace
 
 int launch_filter(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int split_terms, bool adjoint,
-                  cudaStream_t stream, unsigned int *view_max)
+                  cudaStream_t stream, unsigned int *view_max, int view_begin, int view_count)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return IFDK_ERR_CUDA;
     (void)split_terms;
-    if (adjoint) return launch_simt<float, true>(p, E, Q, stream);
+    if (view_count < 0) view_count = p->g.np - view_begin;
+    if (view_count == 0) return IFDK_OK;
+    const int b = view_begin, n = view_count;
+    if (adjoint) return launch_simt<float, true>(p, E, Q, stream, nullptr, b, n);
     switch (q_dtype) {
-    case IFDK_F32: return launch_simt<float, false>(p, E, Q, stream, view_max);
-    case IFDK_F16: return launch_simt<__half, false>(p, E, Q, stream, view_max);
-    default: return launch_simt<__nv_bfloat16, false>(p, E, Q, stream, view_max);
+    case IFDK_F32: return launch_simt<float, false>(p, E, Q, stream, view_max, b, n);
+    case IFDK_F16: return launch_simt<__half, false>(p, E, Q, stream, view_max, b, n);
+    default: return launch_simt<__nv_bfloat16, false>(p, E, Q, stream, view_max, b, n);
     }
 }
 

@@ -373,13 +373,15 @@ int encode_bf16_3d(CUtensorMap *m, const void *base, uint64_t kpad, uint64_t row
 // Data planes of split s.
 int data_planes(int terms) { return terms; }
 
+// E, Q: views [view_begin, view_begin + view_count) (row 0 = row 0 of view view_begin)
 template <typename TQ>
 int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size_t ws_bytes, unsigned int *view_max,
-              cudaStream_t stream)
+              cudaStream_t stream, int view_begin, int view_count)
 {
     const ifdk_geometry &g = p->g;
     const int kpad = p->tc_kpad, npad = p->tc_npad, planes = data_planes(terms);
-    const long long rows = (long long)g.np * g.nv;
+    const long long rows = (long long)view_count * g.nv;
+    const float *sweight = p->d_sweight ? p->d_sweight + (size_t)view_begin * g.nu : nullptr;
     const size_t row_bytes = (size_t)planes * kpad * 2;
     long long cap = (long long)(ws_bytes / row_bytes) / kTcM * kTcM;
     if (cap < kTcM) return IFDK_ERR_INVALID;
@@ -401,14 +403,14 @@ int launch_tc(ifdk_plan_s *p, const float *E, void *Q, int terms, void *ws, size
     a.nk = kpad / kTcK;
     a.npairs = terms == 3 ? 6 : (terms == 2 ? 3 : 1);
     a.planes = planes;
-    a.view_max = view_max;
+    a.view_max = view_max ? view_max + view_begin : nullptr;
     a.nv = g.nv;
     a.stages = tc_stages(planes);
     for (long long r0 = 0; r0 < rows; r0 += cap) {
         const int nr = (int)(rows - r0 < cap ? rows - r0 : cap);
         const long long threads = (long long)nr * (kpad / 8);
         filter_split_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(
-            E, p->d_fcos, p->d_fcos_lo, p->d_sweight, static_cast<__nv_bfloat16 *>(ws), g.nu, g.nv, kpad, r0, nr,
+            E, p->d_fcos, p->d_fcos_lo, sweight, static_cast<__nv_bfloat16 *>(ws), g.nu, g.nv, kpad, r0, nr,
             planes, cap * kpad);
         a.row0 = r0;
         a.nrows = nr;
@@ -456,12 +458,15 @@ size_t filter_workspace_min(const ifdk_plan_s *p, int terms)
 }
 
 int launch_filter_tc(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int terms, void *ws, size_t ws_bytes,
-                     cudaStream_t stream, unsigned int *view_max)
+                     cudaStream_t stream, unsigned int *view_max, int view_begin, int view_count)
 {
+    if (view_count < 0) view_count = p->g.np - view_begin;
+    if (view_count == 0) return IFDK_OK;
     switch (q_dtype) {
-    case IFDK_F32: return launch_tc<float>(p, E, Q, terms, ws, ws_bytes, view_max, stream);
-    case IFDK_F16: return launch_tc<__half>(p, E, Q, terms, ws, ws_bytes, view_max, stream);
-    default: return launch_tc<__nv_bfloat16>(p, E, Q, terms, ws, ws_bytes, view_max, stream);
+    case IFDK_F32: return launch_tc<float>(p, E, Q, terms, ws, ws_bytes, view_max, stream, view_begin, view_count);
+    case IFDK_F16: return launch_tc<__half>(p, E, Q, terms, ws, ws_bytes, view_max, stream, view_begin, view_count);
+    default:
+        return launch_tc<__nv_bfloat16>(p, E, Q, terms, ws, ws_bytes, view_max, stream, view_begin, view_count);
     }
 }
 

@@ -131,13 +131,15 @@ void plan_backproject(ifdk_plan_s *p);
 // Q holds views [q_view0, q_view0 + q_views) of [nv][nu] each.
 int launch_backproject(ifdk_plan_s *p, const void *Q, int q_dtype, int view_begin, int view_count, int q_view0,
                        int q_views, float *vol, cudaStream_t stream);
+// E, Q hold views [view_begin, view_begin + view_count) (view_count < 0: to the last view)
 int launch_filter(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int split_terms, bool adjoint,
-                  cudaStream_t stream, unsigned int *view_max = nullptr);
+                  cudaStream_t stream, unsigned int *view_max = nullptr, int view_begin = 0, int view_count = -1);
 int plan_filter_tc(ifdk_plan_s *p);
 size_t filter_workspace_min(const ifdk_plan_s *p, int terms);
 // view_max (optional): device [np] bits of max |Q| per view, zeroed by the caller
 int launch_filter_tc(ifdk_plan_s *p, const float *E, void *Q, int q_dtype, int terms, void *ws, size_t ws_bytes,
-                     cudaStream_t stream, unsigned int *view_max = nullptr);
+                     cudaStream_t stream, unsigned int *view_max = nullptr, int view_begin = 0,
+                     int view_count = -1);
 int launch_project(ifdk_plan_s *p, const float *vol, float *P, int view_begin, int view_count,
                    cudaStream_t stream);
 int launch_wait_selftest(ifdk_plan_s *p, unsigned long long ns, cudaStream_t stream);

@@ -242,8 +242,9 @@ int ifdk_destroy(ifdk_plan p)
 
 namespace {
 // ifdk_filter and ifdk_filter_max; view_max: nullptr, or [np] zeroed on the stream
+// E, Q hold views [view_begin, view_begin + view_count) (the whole scan: 0, np)
 int filter_call(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_terms, void *workspace,
-                size_t workspace_bytes, float *view_max, void *stream)
+                size_t workspace_bytes, float *view_max, void *stream, int view_begin = 0, int view_count = -1)
 {
     if (!p || !E || !Q) return IFDK_ERR_INVALID;
     if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
@@ -258,8 +259,10 @@ int filter_call(ifdk_plan p, const float *E, void *Q, int q_dtype, int split_ter
     unsigned int *vm = reinterpret_cast<unsigned int *>(view_max);
     if (vm && cudaMemsetAsync(vm, 0, sizeof(unsigned int) * p->g.np, (cudaStream_t)stream) != cudaSuccess)
         return IFDK_ERR_CUDA;
-    if (split_terms == 0) return launch_filter(p, E, Q, q_dtype, 0, false, (cudaStream_t)stream, vm);
-    return launch_filter_tc(p, E, Q, q_dtype, split_terms, workspace, workspace_bytes, (cudaStream_t)stream, vm);
+    if (split_terms == 0)
+        return launch_filter(p, E, Q, q_dtype, 0, false, (cudaStream_t)stream, vm, view_begin, view_count);
+    return launch_filter_tc(p, E, Q, q_dtype, split_terms, workspace, workspace_bytes, (cudaStream_t)stream, vm,
+                            view_begin, view_count);
 }
 }  // namespace
 
@@ -274,6 +277,16 @@ int ifdk_filter_max(ifdk_plan p, const float *E, void *Q, int q_dtype, int split
 {
     if (!view_max) return IFDK_ERR_INVALID;
     return filter_call(p, E, Q, q_dtype, split_terms, workspace, workspace_bytes, view_max, stream);
+}
+
+int ifdk_filter_views(ifdk_plan p, const float *Ev, void *Qv, int q_dtype, int split_terms, int view_begin,
+                      int view_count, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!p || view_begin < 0 || view_count < 0 || view_begin > p->g.np || view_count > p->g.np - view_begin)
+        return IFDK_ERR_INVALID;
+    if (view_count == 0) return IFDK_OK;
+    return filter_call(p, Ev, Qv, q_dtype, split_terms, workspace, workspace_bytes, nullptr, stream, view_begin,
+                       view_count);
 }
 
 int ifdk_filter_workspace_size(ifdk_plan p, int split_terms, size_t *min_bytes, size_t *preferred_bytes)
@@ -362,6 +375,26 @@ int ifdk_backproject_packed_pairs(ifdk_plan p, const void *Qp, int q_dtype, int 
     zr.nz_out = 2 * pair_count - ((p->g.nz & 1) && pair_begin + pair_count == npairs ? 1 : 0);
     return launch_backproject_packed(p, Qp, q_dtype, view_begin, view_count, 0, p->g.np, vol, (cudaStream_t)stream,
                                      zr);
+}
+
+int ifdk_backproject_packed_batch(ifdk_plan p, const void *Qpb, int q_dtype, int view_begin, int view_count,
+                                  float *vol, void *stream)
+{
+    int rc = check_backproject_args(p, Qpb, q_dtype, view_begin, view_count, vol);
+    if (rc != IFDK_OK) return rc;
+    if (!p->pk[q_dtype].path) return IFDK_ERR_UNSUPPORTED;
+    const int h = p->g.np / 2;
+    if (p->g.np % 2 != 0 || view_begin + view_count > h) return IFDK_ERR_INVALID;
+    if (view_count == 0) return IFDK_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return IFDK_ERR_CUDA;
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int n = view_count, b = view_begin;
+    // packed view q of the batch is view b + q for q < n, view b + h + q - n after
+    if (p->use_half_turn && p->pk2[q_dtype].path) return launch_packed_pairs(p, Qpb, q_dtype, b, n, b, n, 2 * n, vol, s);
+    rc = launch_backproject_packed(p, Qpb, q_dtype, b, n, b, 2 * n, vol, s);
+    if (rc == IFDK_OK) rc = launch_backproject_packed(p, Qpb, q_dtype, b + h, n, b + h - n, 2 * n, vol, s);
+    return rc;
 }
 
 int ifdk_set_view_pairing(ifdk_plan p, int enable)

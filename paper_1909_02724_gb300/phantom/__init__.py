@@ -151,6 +151,28 @@ def line_integrals(ell: Ellipsoids, geom: Geometry, views=None) -> np.ndarray:
     return out
 
 
+def line_integral_rows(ell: Ellipsoids, geom: Geometry, s_idx: np.ndarray, r_idx: np.ndarray,
+                       threads: int | None = None, chunk: int = 32) -> np.ndarray:
+    """E[s_idx[n]][r_idx[n]][:] for selected detector rows (FP64): the same chords as
+    line_integrals, for many views at once (rows in chunks over host threads)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    s_idx, r_idx = np.asarray(s_idx), np.asarray(r_idx)
+    out = np.empty((len(s_idx), geom.nu))
+    iu = np.arange(geom.nu)
+
+    def work(a):
+        b = min(a + chunk, len(s_idx))
+        for s in np.unique(s_idx[a:b]):
+            sel = a + np.nonzero(s_idx[a:b] == s)[0]
+            src = source_positions(geom, [s])[0]
+            out[sel] = chord_lengths(ell, src, pixel_positions(geom, geom.angles[s], iu[None, :], r_idx[sel][:, None]))
+
+    with ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
+        list(ex.map(work, range(0, len(s_idx), chunk)))
+    return out
+
+
 def add_noise(E: np.ndarray, rel_sigma: float, seed: int) -> np.ndarray:
     """Gaussian noise with sigma = rel_sigma * max(E), seeded."""
     rng = np.random.default_rng(seed)
