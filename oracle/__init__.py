@@ -15,6 +15,10 @@ follows (Chen et al., SC'19, arXiv 1909.02724):
 * ``backproject``, ``backproject_voxels`` -- Algorithm 2 with Algorithm 3
 * ``project`` -- the exact adjoint of ``backproject``
 * ``volume_slices`` -- the output stage of Algorithm 4 (I <- reshape(I~)), in numpy
+* ``sart``, ``mlem`` -- the iterative solvers the paper names as further users of
+  its back-projector (Sec. 1 and Sec. 6: SART, Andersen & Kak 1984; MLEM, Shepp &
+  Vardi 1982), in numpy on ``project`` (A) and ``backproject`` (A^T), with
+  ordered view subsets (Hudson & Larkin 1994)
 * ``parker_weight``, ``short_scan_weights`` -- short-scan redundancy weights
   (Parker, Med. Phys. 9, 1982; not in the paper), in numpy; ``filter_rows`` /
   ``filter_views`` apply them for geometries with ``short_scan`` set
@@ -325,3 +329,94 @@ def volume_slices(vol: np.ndarray, k_begin: int = 0, k_count: int | None = None,
     if dtype == "bf16":
         return round_bf16_bits(out)
     raise ValueError(dtype)
+
+
+# --------------------------------------------------------------------------
+# Iterative solvers on the back-projection / adjoint pair.  The system matrix
+# is A = project (volume -> views, the exact adjoint of the back-projection)
+# and A^T = backproject.  A subset is a list of (view_begin, view_count)
+# ranges; an iteration visits the subsets in order.
+# --------------------------------------------------------------------------
+
+def _project_ranges(geom, x, ranges, threads=None):
+    out = np.zeros((geom.np, geom.nv, geom.nu))
+    for b, c in ranges:
+        project(geom, x, b, c, out=out, threads=threads)
+    return out
+
+
+def _backproject_ranges(geom, q, ranges, threads=None):
+    vol = np.zeros((geom.nx, geom.ny, geom.nz))
+    for b, c in ranges:
+        backproject(geom, q, b, c, vol=vol, threads=threads)
+    return vol
+
+
+def _views_of(ranges, np_):
+    m = np.zeros(np_, dtype=bool)
+    for b, c in ranges:
+        m[b:b + c] = True
+    return m
+
+
+def column_sums(geom, ranges, threads=None) -> np.ndarray:
+    """C_S = A_S^T 1: the back-projection of all-ones views over the subset's views."""
+    return _backproject_ranges(geom, np.ones((geom.np, geom.nv, geom.nu)), ranges, threads)
+
+
+def row_sums(geom, threads=None) -> np.ndarray:
+    """R = A 1: the projection of an all-ones volume (every view)."""
+    return project(geom, np.ones((geom.nx, geom.ny, geom.nz)), threads=threads)
+
+
+def sart(geom, p: np.ndarray, x0: np.ndarray, iterations: int, subsets, lam: float = 1.0,
+         nonneg: bool = False, threads=None) -> list:
+    """SART (Andersen & Kak, Ultrasonic Imaging 6, 1984), block form over ordered
+    view subsets: for each subset S in turn,
+        x <- x + lam * (A_S^T ((p - A x) / R)) / C_S
+    with R = A 1 (row sums over every voxel) and C_S = A_S^T 1 (column sums over
+    the subset's rays); a ray with R = 0 contributes nothing, a voxel with
+    C_S = 0 is left as it is; nonneg clips x at 0 after each update.  One
+    subset holding every view is SIRT.  Returns the iterate after each
+    iteration (a pass over all subsets)."""
+    R = row_sums(geom, threads)
+    Cs = [column_sums(geom, S, threads) for S in subsets]
+    x = np.array(x0, dtype=np.float64, copy=True)
+    out = []
+    for _ in range(iterations):
+        for S, C in zip(subsets, Cs):
+            m = _views_of(S, geom.np)
+            Ax = _project_ranges(geom, x, S, threads)
+            r = np.zeros_like(Ax)
+            np.divide(p - Ax, R, out=r, where=(R > 0) & m[:, None, None])
+            U = _backproject_ranges(geom, r, S, threads)
+            step = np.zeros_like(x)
+            np.divide(U, C, out=step, where=C > 0)
+            x = x + lam * step
+            if nonneg:
+                x = np.maximum(x, 0.0)
+        out.append(x.copy())
+    return out
+
+
+def mlem(geom, p: np.ndarray, x0: np.ndarray, iterations: int, subsets, threads=None) -> list:
+    """MLEM (Shepp & Vardi, IEEE TMI 1, 1982) over ordered view subsets (OS-EM,
+    Hudson & Larkin, IEEE TMI 13, 1994): for each subset S in turn,
+        x <- x * (A_S^T (p / A x)) / C_S
+    with C_S = A_S^T 1; a ray with A x = 0 contributes nothing, a voxel with
+    C_S = 0 is left as it is.  p >= 0, x0 > 0.  Returns the iterate after each
+    iteration."""
+    Cs = [column_sums(geom, S, threads) for S in subsets]
+    x = np.array(x0, dtype=np.float64, copy=True)
+    out = []
+    for _ in range(iterations):
+        for S, C in zip(subsets, Cs):
+            m = _views_of(S, geom.np)
+            Ax = _project_ranges(geom, x, S, threads)
+            ratio = np.zeros_like(Ax)
+            np.divide(p, Ax, out=ratio, where=(Ax > 0) & m[:, None, None])
+            U = _backproject_ranges(geom, ratio, S, threads)
+            upd = x * U
+            x = np.where(C > 0, upd / np.where(C > 0, C, 1.0), x)
+        out.append(x.copy())
+    return out
