@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--batches", type=int, default=4,
                     help="batches of half-turn view pairs per reconstruction (a step is one batch)")
     ap.add_argument("--no-arms", action="store_true", help="skip the other storage types' arms")
+    ap.add_argument("--solver", choices=["sart", "mlem"], default=None,
+                    help="time iterations of an iterative solver instead of FDK (e.g. --workload grad256)")
+    ap.add_argument("--subsets", type=int, default=10, help="ordered view subsets of --solver")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
@@ -210,13 +213,20 @@ def oracle_sample_fdk(g, E_rows, s_idx, r_idx, vox, threads: int):
     """Oracle FDK at the voxels vox from the raw rows E_rows of (view s_idx, row
     r_idx): Algorithm 1 on those rows, then Algorithm 2 at each voxel.  Returns
     (values, seconds)."""
+    vals, t_f, t_b = oracle_sample_fdk_parts(g, E_rows, s_idx, r_idx, vox, threads)
+    return vals, t_f + t_b
+
+
+def oracle_sample_fdk_parts(g, E_rows, s_idx, r_idx, vox, threads: int):
+    """oracle_sample_fdk with the two stages timed apart: (values, filter s, back-projection s)."""
     import oracle
     t0 = time.perf_counter()
     Qs = oracle.filter_rows(g, E_rows, r_idx, threads=threads)
+    t1 = time.perf_counter()
     rowmap = -np.ones((g.np, g.nv), dtype=np.int64)
     rowmap[s_idx, r_idx] = np.arange(len(s_idx))
     vals = oracle.backproject_voxels(g, Qs, vox, rowmap=rowmap, threads=threads)
-    return vals, time.perf_counter() - t0
+    return vals, t1 - t0, time.perf_counter() - t1
 
 
 def run_reference(args):
@@ -626,17 +636,21 @@ def cpu_baseline(w, E) -> dict:
     s_idx, r_idx = midplane_rows(g)
     E_rows = E[torch.from_numpy(s_idx).to(E.device), torch.from_numpy(r_idx).to(E.device)].double().cpu().numpy()
     out = {"unit": UNIT, "kind": "oracle"}
-    for label, threads in (("all_cores", cores), ("one_thread", 1)):
+    for label, threads, budget in (("all_cores", cores, 10.0), ("one_thread", 1, 20.0)):
+        # size the back-projection part of the sample to about `budget` seconds
         n = min(len(vox_all), 4096 * threads)
-        _, dt = oracle_sample_fdk(g, E_rows, s_idx, r_idx, vox_all[:n], threads)
-        n = int(min(len(vox_all), max(256, n * 10.0 / max(dt, 1e-3))))
-        _, dt = oracle_sample_fdk(g, E_rows, s_idx, r_idx, vox_all[:n], threads)
-        out[label] = {"value": n * g.np / dt / 2 ** 30, "threads": threads, "voxels": n, "seconds": dt}
+        _, t_f, t_b = oracle_sample_fdk_parts(g, E_rows, s_idx, r_idx, vox_all[:n], threads)
+        n = int(min(len(vox_all), max(256, n * max(budget - t_f, 1.0) / max(t_b, 1e-3))))
+        _, t_f, t_b = oracle_sample_fdk_parts(g, E_rows, s_idx, r_idx, vox_all[:n], threads)
+        out[label] = {"value": n * g.np / (t_f + t_b) / 2 ** 30, "threads": threads, "voxels": n,
+                      "seconds": t_f + t_b, "filter_seconds": t_f, "rows_filtered": int(len(s_idx)),
+                      "backprojection_gups": n * g.np / t_b / 2 ** 30}
     out["value"] = out["all_cores"]["value"]
     out["cores"] = cores
     out["sample"] = (f"seeded voxels of the two mid-plane z-slices x all {g.np} views (all_cores: "
                      f"{out['all_cores']['voxels']}, one_thread: {out['one_thread']['voxels']} voxels), incl. "
-                     f"filtering the detector rows they touch (FP64 C, pthreads)")
+                     f"filtering the {len(s_idx)} detector rows they touch (FP64 C, pthreads); "
+                     f"backprojection_gups leaves the filtering out")
     return out
 
 
@@ -742,10 +756,87 @@ def run_slab(args):
     print(json.dumps(line), flush=True)
 
 
+def run_solver(args):
+    """--solver sart|mlem: iterations of the iterative solver on the workload's
+    projections (one GPU); a step is one iteration (a pass over the subsets)."""
+    import torch
+    from paper_1909_02724_gb300 import binding as B
+    from paper_1909_02724_gb300.api import IterativeSolver
+    from paper_1909_02724_gb300.build import build
+    from paper_1909_02724_gb300.phantom import workload, workload_projections_gpu
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    build()
+    w = workload(args.workload)
+    g = w.geom
+    plan = B.Plan(g)
+    p = workload_projections_gpu(w)
+    if args.solver == "mlem":
+        p.clamp_(min=0.0)
+    solver = IterativeSolver(plan, args.solver, args.subsets, lam=1.0, nonneg=args.solver == "sart")
+    x = torch.zeros((g.nx, g.ny, g.nz), dtype=torch.float32, device="cuda")
+    x0 = 0.0 if args.solver == "sart" else 1.0
+    x.fill_(x0)
+    solver.run(p, x, max(1, args.warmup))
+    x.fill_(x0)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    stream = torch.cuda.current_stream()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    time.sleep(0.3)
+    t0.record(stream)
+    solver.run(p, x, args.steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    # one subset update timed stage by stage
+    S, C = solver.sets[0], solver.C[0]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    ev[0].record(stream)
+    for b, c in S:
+        plan.project(x, solver.Ax, view_begin=b, view_count=c)
+    ev[1].record(stream)
+    o = 0
+    for b, c in S:
+        B.ifdk_iter_ratio(plan.handle, solver.method, p[b:b + c], solver.Ax[b:b + c],
+                          None if solver.R is None else solver.R[b:b + c], solver.rb[o:o + c], c)
+        o += c
+    ev[2].record(stream)
+    solver._backproject(S, solver.U)
+    ev[3].record(stream)
+    B.ifdk_iter_update(plan.handle, solver.method, x, solver.U, C, 1.0, solver.nonneg)
+    ev[4].record(stream)
+    torch.cuda.synchronize()
+    stages = dict(zip(("project", "ratio", "backproject", "update"),
+                      (ev[i].elapsed_time(ev[i + 1]) for i in range(4))))
+    upd = 2 * g.nx * g.ny * g.nz * g.np
+    views_s = sum(c for _, c in S)
+    line = {"metric": f"{args.solver} iteration GUPS (forward + back-projection updates, 2 Nx Ny Nz Np per "
+                      "iteration / T / 2^30)",
+            "value": upd / (ms * 1e-3) / 2 ** 30, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(w), "solver": args.solver, "subsets": len(solver.sets),
+                       "bp_path": "packed batch" if solver.packed else "filtered views as stored",
+                       "step": "one iteration: every subset's project, ratio, back-projection and update"},
+            "first_subset_ms": stages, "first_subset_views": views_s,
+            "project_gups": g.nx * g.ny * g.nz * views_s / (stages["project"] * 1e-3) / 2 ** 30,
+            "backproject_gups": g.nx * g.ny * g.nz * views_s / (stages["backproject"] * 1e-3) / 2 ** 30,
+            "clocks": ck}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.solver:
+        run_solver(args)
     elif args.workload == "slab4096":
         run_slab(args)
     else:

@@ -379,6 +379,34 @@ int ifdk_view_split(ifdk_plan p, int q_dtype, int *splits);
 int ifdk_project(ifdk_plan p, const float *vol, float *P, int view_begin, int view_count,
                  void *stream);
 
+/* Element-wise steps of the iterative solvers that reuse the back-projection
+   and its adjoint (Sec. 1 and Sec. 6 name SART and MLEM as users of the
+   back-projector): with A = ifdk_project and A^T the back-projection, one
+   update over a subset S of the views is
+     SART (Andersen & Kak 1984):  x <- x + lambda A_S^T((p - A x) / R) / C_S
+     MLEM (Shepp & Vardi 1982; ordered subsets, Hudson & Larkin 1994):
+                                  x <- x A_S^T(p / A x) / C_S
+   with R = A 1 (ray sums over every voxel) and C_S = A_S^T 1 (voxel sums over
+   the subset's rays).  A ray with R = 0 (SART) or A x = 0 (MLEM) gives 0; a
+   voxel with C_S = 0 keeps its value.  The caller sequences the steps:
+   ifdk_project of x over S's views into Ax (zeroed), ifdk_iter_ratio,
+   a back-projection of the ratios into U (zeroed), ifdk_iter_update.
+   ifdk_iter_ratio: Pm (measured views), Ax (A x), R (row sums; SART only,
+   may be NULL for MLEM) and out are device FP32 arrays of view_count views
+   [view_count][nv][nu] (pointers to the range's first view); out receives
+   the ratio and Ax is set to 0 (ready for the next projection).
+   ifdk_iter_update: x, U (the back-projected ratios) and C (C_S) are device
+   FP32 [nx][ny][nz]; x is updated in place and U set to 0; nonneg = 1
+   clips SART's x at 0 (ignored by MLEM, which keeps x >= 0 for p >= 0).
+   Buffers 4-byte aligned (16-byte alignment takes the vector path), owned by
+   the caller, not overlapping.  method: IFDK_SART or IFDK_MLEM.  One
+   streaming pass each, asynchronous on `stream`. */
+enum { IFDK_SART = 0, IFDK_MLEM = 1 };
+int ifdk_iter_ratio(ifdk_plan p, int method, const float *Pm, float *Ax, const float *R, float *out,
+                    int view_count, void *stream);
+int ifdk_iter_update(ifdk_plan p, int method, float *x, float *U, const float *C, float lambda, int nonneg,
+                     void *stream);
+
 /* Output stage of Algorithm 4, I <- reshape(I~) (Sec. 3.3; the volume is
    stored as Nz slices of Nx x Ny, Sec. 4): writes slices [k_begin,
    k_begin + k_count) of the k-fastest volume vol (device FP32 [nx][ny][nz],

@@ -4,7 +4,8 @@
 buffers: it copies the projections in (from pinned memory), filters,
 back-projects and copies the volume out, all on one stream.  ``BatchFdk``
 reconstructs in batches of half-turn view pairs and ``batch_host_pipeline``
-streams those batches from host memory.  When the plan
+streams those batches from host memory.  ``IterativeSolver`` runs SART or MLEM
+on the back-projection and its adjoint.  When the plan
 has packed views (centred volume, 2 v_c integral) and a packed buffer is
 given or allowed, the filtered views are packed (ifdk_pack_views) and
 back-projected by the packed kernel; otherwise by ifdk_backproject.  Every
@@ -222,6 +223,102 @@ def batch_host_pipeline(bf: BatchFdk, E_host: torch.Tensor, vol_host: torch.Tens
     s_out.synchronize()
     s_c.synchronize()
     return vol_host
+
+
+def half_turn_subsets(n_views: int, subsets: int) -> list:
+    """Ordered subsets of the views for the iterative solvers, each a list of
+    (view_begin, view_count) ranges: with an even view count, subset b is the
+    block of half-turn pairs [b n, b n + n) and [np/2 + b n, np/2 + b n + n),
+    n = ceil(np / (2 subsets)) (so that the packed batch back-projection serves
+    it); with an odd count, contiguous blocks of ceil(np / subsets) views."""
+    if subsets < 1:
+        raise ValueError("subsets must be positive")
+    if n_views % 2 == 0:
+        h = n_views // 2
+        n = -(-h // subsets)
+        return [[(b * n, min(n, h - b * n)), (h + b * n, min(n, h - b * n))] for b in range(subsets) if b * n < h]
+    m = -(-n_views // subsets)
+    return [[(b * m, min(m, n_views - b * m))] for b in range(subsets) if b * m < n_views]
+
+
+class IterativeSolver:
+    """SART or MLEM over ordered view subsets on the GPU, the iterative methods
+    the paper names as users of its back-projector (Sec. 1, Sec. 6): A is
+    ifdk_project, A^T the back-projection (the packed batch kernel for
+    half-turn pair subsets, ifdk_backproject_views otherwise), and the update
+    steps are ifdk_iter_ratio / ifdk_iter_update:
+        SART:  x <- x + lam A_S^T((p - A x) / R) / C_S     (R = A 1, C_S = A_S^T 1)
+        MLEM:  x <- x A_S^T(p / A x) / C_S
+    R and the C_S are computed once, here.  Buffers: the forward projection
+    (all views, kept zeroed between uses by ifdk_iter_ratio), one subset of
+    ratios (and its packed views), the back-projected ratios (kept zeroed by
+    ifdk_iter_update), and one C_S volume per subset."""
+
+    def __init__(self, plan: Plan, method: str = "sart", subsets: int = 1, lam: float = 1.0, nonneg: bool = False,
+                 device=None, packed: bool = True):
+        from .binding import IFDK_MLEM, IFDK_SART
+        g = plan.geom
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        if method not in ("sart", "mlem"):
+            raise ValueError("method must be 'sart' or 'mlem'")
+        self.plan, self.lam, self.nonneg = plan, float(lam), bool(nonneg)
+        self.method = IFDK_SART if method == "sart" else IFDK_MLEM
+        self.sets = half_turn_subsets(g.np, subsets)
+        self.packed = packed and g.np % 2 == 0 and plan.has_packed(torch.float32)
+        nmax = max(sum(c for _, c in S) for S in self.sets)
+        self.Ax = torch.zeros((g.np, g.nv, g.nu), dtype=torch.float32, device=dev)
+        self.rb = torch.empty((nmax, g.nv, g.nu), dtype=torch.float32, device=dev)
+        self.Qp = (torch.empty((nmax,) + plan.packed_shape(torch.float32)[1:], dtype=torch.float32, device=dev)
+                   if self.packed else None)
+        self.U = torch.zeros((g.nx, g.ny, g.nz), dtype=torch.float32, device=dev)
+        self.R = plan.project(torch.ones((g.nx, g.ny, g.nz), dtype=torch.float32, device=dev)) \
+            if self.method == IFDK_SART else None
+        self.C = []
+        for S in self.sets:
+            self.rb.fill_(1.0)
+            c = torch.zeros_like(self.U)
+            self._backproject(S, c)
+            self.C.append(c)
+
+    def _backproject(self, S, vol, stream=None) -> None:
+        """vol += A_S^T of the ratios in self.rb (the subset's views in range order)."""
+        if self.packed and len(S) == 2 and S[1][0] == S[0][0] + self.plan.geom.np // 2 and S[0][1] == S[1][1]:
+            n = S[0][1]
+            self.plan.pack(self.rb[:2 * n], self.Qp[:2 * n], stream=stream)
+            self.plan.backproject_packed_batch(self.Qp[:2 * n], S[0][0], n, vol, stream=stream)
+            return
+        o = 0
+        for b, c in S:
+            self.plan.backproject_views(self.rb[o:o + c], vol, view_begin=b, stream=stream)
+            o += c
+
+    def update(self, p: torch.Tensor, x: torch.Tensor, S, C, stream=None) -> None:
+        """One subset update of x in place (p: float32 CUDA [np][nv][nu] measured views)."""
+        from .binding import ifdk_iter_ratio, ifdk_iter_update
+        for b, c in S:
+            self.plan.project(x, self.Ax, view_begin=b, view_count=c, stream=stream)
+        o = 0
+        for b, c in S:
+            ifdk_iter_ratio(self.plan.handle, self.method, p[b:b + c], self.Ax[b:b + c],
+                            None if self.R is None else self.R[b:b + c], self.rb[o:o + c], c, stream)
+            o += c
+        self._backproject(S, self.U, stream=stream)
+        ifdk_iter_update(self.plan.handle, self.method, x, self.U, C, self.lam, self.nonneg, stream)
+
+    def run(self, p: torch.Tensor, x: torch.Tensor, iterations: int, keep: bool = False, stream=None):
+        """iterations passes over the subsets, x updated in place; keep: return a copy of
+        x after every pass (else the list is empty)."""
+        g = self.plan.geom
+        if tuple(p.shape) != (g.np, g.nv, g.nu) or p.dtype != torch.float32 or not p.is_contiguous():
+            raise ValueError(f"p must be a contiguous float32 CUDA tensor of shape {(g.np, g.nv, g.nu)}")
+        self.plan._check_vol(x)
+        out = []
+        for _ in range(iterations):
+            for S, C in zip(self.sets, self.C):
+                self.update(p, x, S, C, stream=stream)
+            if keep:
+                out.append(x.clone())
+        return out
 
 
 def volume_slices_host(plan: Plan, vol: torch.Tensor, out_host: torch.Tensor, chunk_slices: int = 64,

@@ -35,7 +35,7 @@ EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_
            "ifdk_backproject_packed_info", "ifdk_query_packed", "ifdk_volume_slices",
            "ifdk_set_view_split", "ifdk_view_split", "ifdk_filter_max", "ifdk_set_short_scan",
            "ifdk_backproject_packed_pairs", "ifdk_filter_views", "ifdk_backproject_packed_batch",
-           "ifdk_arith_rate")
+           "ifdk_arith_rate", "ifdk_iter_ratio", "ifdk_iter_update")
 
 
 class IfdkError(RuntimeError):
@@ -106,6 +106,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.ifdk_view_split.argtypes = [vp, i32, ctypes.POINTER(i32)]
         lib.ifdk_filter_views.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp, ctypes.c_size_t, vp]
         lib.ifdk_backproject_packed_batch.argtypes = [vp, vp, i32, i32, i32, vp, vp]
+        lib.ifdk_iter_ratio.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp]
+        lib.ifdk_iter_update.argtypes = [vp, i32, vp, vp, vp, ctypes.c_float, i32, vp]
         lib.ifdk_arith_rate.argtypes = [i32, i32, ctypes.c_longlong, vp, vp, ctypes.POINTER(i64), vp]
         lib.ifdk_status_string.argtypes = [i32]
         lib.ifdk_status_string.restype = ctypes.c_char_p
@@ -277,6 +279,21 @@ def ifdk_backproject_packed_batch(plan: int, Qpb, q_dtype: int, view_begin: int,
     _check(load_library().ifdk_backproject_packed_batch(plan, _addr(Qpb), int(q_dtype), int(view_begin),
                                                         int(view_count), _addr(vol), _stream(stream)),
            "ifdk_backproject_packed_batch")
+
+
+IFDK_SART, IFDK_MLEM = 0, 1
+
+
+def ifdk_iter_ratio(plan: int, method: int, Pm, Ax, R, out, view_count: int, stream=None) -> None:
+    """SART / MLEM ray-space ratio over view_count views (pointers at the range's first view)."""
+    _check(load_library().ifdk_iter_ratio(plan, int(method), _addr(Pm), _addr(Ax), _addr(R), _addr(out),
+                                          int(view_count), _stream(stream)), "ifdk_iter_ratio")
+
+
+def ifdk_iter_update(plan: int, method: int, x, U, C, lam: float, nonneg: bool, stream=None) -> None:
+    """SART / MLEM volume update x <- ..., U cleared."""
+    _check(load_library().ifdk_iter_update(plan, int(method), _addr(x), _addr(U), _addr(C), float(lam),
+                                           int(bool(nonneg)), _stream(stream)), "ifdk_iter_update")
 
 
 def ifdk_arith_rate(kind: int, blocks: int, iters: int, sink, clocks, stream=None) -> tuple[int, int]:

@@ -24,7 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
            "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
 LIB_SOURCES = ["ifdk_plan.cu", "ifdk_bp.cu", "ifdk_bp_packed.cu", "ifdk_filter.cu", "ifdk_filter_tc.cu", "ifdk_filter_static.cu",
-               "ifdk_rates.cu",
+               "ifdk_rates.cu", "ifdk_iter.cu",
                "ifdk_project.cu", "ifdk_stream.cu", "ifdk_volume.cu"]
 PHANTOM_SOURCES = [os.path.join(PKG, "phantom", "phantom.cu")]
 

@@ -111,7 +111,7 @@ def test_packed_batches_sum_to_the_whole_and_match_the_oracle(dtype, pairing):
 
 
 def test_batch_requests_outside_the_rules_are_refused():
-    g = scaled_geometry(16, 32, 12)
+    g = scaled_geometry(32, 32, 12)
     plan = B.Plan(g)
     Qp = torch.zeros((2 * 4,) + plan.packed_shape(torch.float32)[1:], device="cuda")
     vol = torch.full((g.nx, g.ny, g.nz), 3.0, device="cuda")
@@ -119,7 +119,7 @@ def test_batch_requests_outside_the_rules_are_refused():
         with pytest.raises(B.IfdkError) as e:
             B.ifdk_backproject_packed_batch(plan.handle, Qp, B.IFDK_F32, b, n, vol)
         assert e.value.code == B.IFDK_ERR_INVALID
-    odd = B.Plan(scaled_geometry(16, 32, 13))
+    odd = B.Plan(scaled_geometry(32, 32, 13))
     with pytest.raises(B.IfdkError) as e:
         B.ifdk_backproject_packed_batch(odd.handle, Qp, B.IFDK_F32, 0, 2, vol)
     assert e.value.code == B.IFDK_ERR_INVALID

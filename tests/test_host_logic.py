@@ -348,8 +348,10 @@ def test_every_entry_point_refuses_a_null_plan_before_any_cuda_call():
         for t in fn.argtypes:
             if t in (ctypes.c_int, ctypes.c_int32):
                 args.append(0)
-            elif t in (ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int64):
+            elif t in (ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int64, ctypes.c_longlong):
                 args.append(0)
+            elif t in (ctypes.c_float, ctypes.c_double):
+                args.append(0.0)
             else:
                 args.append(None)
         rc = fn(*args)
