@@ -170,7 +170,10 @@ int ifdk_filter_workspace_size(ifdk_plan p, int split_terms, size_t *min_bytes,
    ifdk_filter with a large workspace.
    Every GPU that loads the library holds the 16 MiB until the process exits.
    The first call on a device looks up the array's device address (with that
-   device current) and should come before any stream capture.  All calls share
+   device current) and should come before any stream capture.  The address is
+   kept for the life of the process: after cudaDeviceReset, or anything else
+   that destroys and recreates the device's primary context, it is stale and
+   this call must not be used again in that process.  All calls share
    the array and it keeps the previous call's contents (nothing in it has to
    start at zero: every row read is written first by the same call); calls
    whose work overlaps on the GPU (other streams, other host threads) race on
@@ -434,6 +437,18 @@ int ifdk_set_wait_limit(ifdk_plan p, uint64_t nanoseconds);
    mbarrier nothing arrives at, for at most `nanoseconds`, then records
    IFDK_ERR_TIMEOUT in the status word and exits cleanly.  Asynchronous. */
 int ifdk_wait_selftest(ifdk_plan p, uint64_t nanoseconds, void *stream);
+
+/* Test hook of the packed back-projection's timeout path (no device fault is
+   involved): with group >= 0, every block of the following packed
+   back-projections on this plan (ifdk_backproject_packed and its pair-range,
+   batch and streaming forms) acts as if its bounded wait for view group
+   `group` (counted from 0 within the launch, two groups per half-turn pair)
+   had run out: it records IFDK_ERR_TIMEOUT in the plan's status word, waits
+   for the copies it issued that may still be landing in its shared memory,
+   and leaves; blocks that start after that skip their work.  The volume's
+   contents are then undefined.  group < 0 turns the hook off (the default).
+   Returns IFDK_ERR_INVALID for a NULL plan. */
+int ifdk_set_test_abort(ifdk_plan p, int group);
 
 /* Describes the launch the plan chose for ifdk_backproject with q_dtype:
    info[0] = path (1 = mirror-pair fold kernel, 0 = general kernel),

@@ -35,7 +35,7 @@ EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_
            "ifdk_backproject_packed_info", "ifdk_query_packed", "ifdk_volume_slices",
            "ifdk_set_view_split", "ifdk_view_split", "ifdk_filter_max", "ifdk_set_short_scan",
            "ifdk_backproject_packed_pairs", "ifdk_filter_views", "ifdk_backproject_packed_batch",
-           "ifdk_arith_rate", "ifdk_iter_ratio", "ifdk_iter_update")
+           "ifdk_arith_rate", "ifdk_iter_ratio", "ifdk_iter_update", "ifdk_set_test_abort")
 
 
 class IfdkError(RuntimeError):
@@ -106,6 +106,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.ifdk_view_split.argtypes = [vp, i32, ctypes.POINTER(i32)]
         lib.ifdk_filter_views.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp, ctypes.c_size_t, vp]
         lib.ifdk_backproject_packed_batch.argtypes = [vp, vp, i32, i32, i32, vp, vp]
+        lib.ifdk_set_test_abort.argtypes = [vp, i32]
         lib.ifdk_iter_ratio.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp]
         lib.ifdk_iter_update.argtypes = [vp, i32, vp, vp, vp, ctypes.c_float, i32, vp]
         lib.ifdk_arith_rate.argtypes = [i32, i32, ctypes.c_longlong, vp, vp, ctypes.POINTER(i64), vp]
@@ -364,6 +365,11 @@ def ifdk_last_device_status(plan: int, stream=None) -> int:
 
 def ifdk_set_wait_limit(plan: int, nanoseconds: int) -> None:
     _check(load_library().ifdk_set_wait_limit(plan, int(nanoseconds)), "ifdk_set_wait_limit")
+
+
+def ifdk_set_test_abort(plan: int, group: int) -> None:
+    """Test hook: packed back-projections act as if the wait for view group `group` ran out (-1: off)."""
+    _check(load_library().ifdk_set_test_abort(plan, int(group)), "ifdk_set_test_abort")
 
 
 def ifdk_wait_selftest(plan: int, nanoseconds: int, stream=None) -> None:

@@ -90,7 +90,16 @@ struct PkArgs {
     // voxels: the direct slab first (k - pair0), then its mirror (the whole volume:
     // pair0 = 0, pair_end = (nz + 1) / 2, nz_out = nz)
     int pair0, pair_end, nz_out;
+    // test hook (ifdk_set_test_abort): every block treats its wait for view group
+    // abort_group as expired (-1: off)
+    int abort_group;
 };
+
+// Bound of the wait an aborting warp spends on the copies it issued that may
+// still be landing in its shared memory: fixed, and independent of the plan's
+// wait limit (which may be short, and has just run out), so that no block
+// leaves while a bulk copy it started can still write to its shared memory.
+constexpr unsigned long long kPkDrainNs = 2000000000ull;
 
 template <typename T> struct PkT;
 template <> struct PkT<float> {
@@ -499,7 +508,7 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
             ok = __shfl_sync(0xffffffffu, e, 0) != 0;
             if (!ok) return;
         }
-        ok = __all_sync(0xffffffffu, mbar_wait_lim(s0 + kPkFull + 8u * st, parity, a.wait_ns));
+        ok = __all_sync(0xffffffffu, t != a.abort_group && mbar_wait_lim(s0 + kPkFull + 8u * st, parity, a.wait_ns));
         if (!ok) return;
         const uint32_t sg = kPkStage0 + (uint32_t)st * a.stage_bytes;
         const float4 *gp = reinterpret_cast<const float4 *>(sm + sg);
@@ -552,7 +561,7 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
             atomicOr(a.status, kStatusTimeout);
             for (int st = 0; st < min(S, ngroups); ++st) {
                 const int t = (int)lds_u32_v(s0 + kPkLast + 4u * st);
-                mbar_wait_lim(s0 + kPkFull + 8u * st, (uint32_t)(t / S) & 1u, a.wait_ns);
+                mbar_wait_lim(s0 + kPkFull + 8u * st, (uint32_t)(t / S) & 1u, kPkDrainNs);
             }
         }
         return;
@@ -754,6 +763,7 @@ int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_beg
     a.terms = p->d_terms;
     a.status = p->d_status;
     a.wait_ns = p->wait_ns;
+    a.abort_group = p->test_abort_group;
     a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
     a.ny_cols = NV == 2 ? g.ny / 2 : g.ny;
     a.tiles_x = (g.nx + kTileX - 1) / kTileX;

@@ -116,6 +116,7 @@ struct ifdk_plan_s {
     size_t split_stride = 0;
     int split_cap = 0, view_split_max = 0, n_sm = 0;
     unsigned long long wait_ns = 2000000000ull;
+    int test_abort_group = -1;           // ifdk_set_test_abort (-1: off)
     // tensor-core filter: Toeplitz matrix as 3 BF16 planes [3][tc_npad][tc_kpad]
     int tc_kpad = 0, tc_npad = 0;
     uint16_t *d_tsplit = nullptr;

@@ -513,6 +513,13 @@ int ifdk_set_wait_limit(ifdk_plan p, uint64_t ns)
     return IFDK_OK;
 }
 
+int ifdk_set_test_abort(ifdk_plan p, int group)
+{
+    if (!p) return IFDK_ERR_INVALID;
+    p->test_abort_group = group < 0 ? -1 : group;
+    return IFDK_OK;
+}
+
 int ifdk_wait_selftest(ifdk_plan p, uint64_t ns, void *stream)
 {
     if (!p || ns == 0 || ns > 10000000000ull) return IFDK_ERR_INVALID;

@@ -139,6 +139,9 @@ def gather_pair_slabs(part, full_vol, nz: int, dst: int = 0):
     import torch
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        # one process holds every pair: the part is the whole volume's pair layout
+        if part.shape[2] != nz:
+            raise ValueError(f"a single process's pair part must hold all {nz} slices, not {part.shape[2]}")
         if full_vol is None:
             full_vol = torch.empty(part.shape[:2] + (nz,), dtype=part.dtype, device=part.device)
         return place_pair_slab(full_vol, part, nz, 0, (nz + 1) // 2)

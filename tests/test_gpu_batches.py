@@ -145,6 +145,7 @@ def test_batch_fdk_matches_the_oracle(dtype, tol):
         vol = torch.zeros((g.nx, g.ny, g.nz), device="cuda")
         bf.reconstruct(Ed, vol)
         torch.cuda.synchronize()
+        assert plan.device_status() == B.IFDK_OK
         v = vol.cpu().numpy()
         assert rel_l2(v, ref) <= tol, (batches, rel_l2(v, ref))
         if dtype == "float32":

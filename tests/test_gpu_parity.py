@@ -157,6 +157,33 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     assert torch.isfinite(vol).all() and float(vol.abs().max()) > 0
 
 
+@pytest.mark.parametrize("name,group", [("fdk64", 3), ("fdk64", 0), ("ragged", 5)])
+def test_packed_kernel_timeout_path_reports_and_recovers(name, group):
+    """The production kernel's timeout branch, reached through the plan's test hook
+    (no device fault): every block treats its wait for one view group as expired,
+    drains its copies in flight and leaves.  The status reads IFDK_ERR_TIMEOUT (then
+    clean), and the next launch, hook off, matches the oracle."""
+    from paper_1909_02724_gb300 import binding as B
+    g = GEOMS[name]
+    p = plan(g)
+    rng = np.random.default_rng(9)
+    Q = rng.normal(size=(g.np, g.nv, g.nu))
+    Qd = torch.from_numpy(Q.astype(np.float32)).cuda()
+    Qp = p.pack(Qd)
+    ref = oracle.backproject(g, Q.astype(np.float32).astype(np.float64))
+    B.ifdk_set_test_abort(p.handle, group)
+    p.backproject_packed(Qp)                                  # whole volume (view split at fdk64)
+    p.backproject_packed_pairs(Qp, 1, 5)                      # a pair range (general instantiation)
+    torch.cuda.synchronize()
+    assert p.device_status() == B.IFDK_ERR_TIMEOUT
+    assert p.device_status() == B.IFDK_OK                     # cleared on read
+    B.ifdk_set_test_abort(p.handle, -1)
+    vol = p.backproject_packed(Qp)
+    v = vol.cpu().numpy()
+    assert p.device_status() == B.IFDK_OK
+    assert rel_l2(v, ref) <= 1e-5 and max_rel(v, ref) <= 1e-4
+
+
 def test_gpu_generator_matches_fp64_generator():
     from paper_1909_02724_gb300.phantom import line_integrals_gpu
     w = workload("fdk64")

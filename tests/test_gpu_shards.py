@@ -52,6 +52,7 @@ def test_view_split_sums_to_whole(world, packed):
             plan.backproject(Qd, part, view_begin=b, view_count=c)
         vol += part
     got = vol.cpu().double().numpy()
+    assert plan.device_status() == 0
     assert rel_l2(got, ref) <= 1e-5
     assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
 

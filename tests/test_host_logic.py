@@ -227,12 +227,17 @@ def check_packed_windows(g, q_dtype, view_pairing=True, blocks=None, pair0=0, pc
         assert ul.min() >= 0.01 and ul.max() < BW - 0.01, (bx, by, bz, ul.min(), ul.max(), BW)
         sig = t["B2"][:, None] * f
         vl = (vc - v0)[:, None, None] + sig[:, :, None] * (kp0 + p)[None, None, :]
+        # box containment of every pair the block computes, written or not: a tail block
+        # runs all Lb pairs, up to Lb - 1 of them past pair0 + pcount (or past the middle)
+        assert vl.shape[-1] == Lb
         assert vl.min() >= 0.01 and vl.max() < H - 1 - 0.01, (bx, by, bz, vl.min(), vl.max(), H)
         # packed element u0a + floor(ul) (column c = element - 1 + 1 ... held from column -1 on)
         cols = u0a[:, None] + np.floor(ul)
         c_in = (cols >= -1) & (cols < -1 + info["row_elems"])
         c_off = (cols + 1 < 0) | (cols >= g.nu)          # both taps c, c + 1 off the detector
         assert np.all(c_in | c_off), (bx, by, bz)
+        # the detector rows behind the taps of the pairs that are written must be packed rows
+        # (a discarded pair's taps only have to stay inside the box, checked above)
         written = (k0 + p) < pair0 + pcount
         rows = v0[:, None, None] + np.floor(vl[:, :, written])
         for rr in (rows, rows + 1):
