@@ -442,7 +442,8 @@ int ifdk_wait_selftest(ifdk_plan p, uint64_t nanoseconds, void *stream);
    involved): with group >= 0, every block of the following packed
    back-projections on this plan (ifdk_backproject_packed and its pair-range,
    batch and streaming forms) acts as if its bounded wait for view group
-   `group` (counted from 0 within the launch, two groups per half-turn pair)
+   `group` (counted from 0 within the block's views: the launch's views, or
+   its share of them under the view split; two groups per half-turn pair)
    had run out: it records IFDK_ERR_TIMEOUT in the plan's status word, waits
    for the copies it issued that may still be landing in its shared memory,
    and leaves; blocks that start after that skip their work.  The volume's
