@@ -93,6 +93,8 @@ struct PkArgs {
     // test hook (ifdk_set_test_abort): every block treats its wait for view group
     // abort_group as expired (-1: off)
     int abort_group;
+    int tiles_y;                        // column tiles along j the grid covers
+    int resident;                       // blocks resident on the GPU at once (SMs x blocks per SM)
 };
 
 // Bound of the wait an aborting warp spends on the copies it issued that may
@@ -409,7 +411,18 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // block coordinates: warp = 16 x 2 patch of columns, 8 warps per 16 x 16 tile
+#if IFDK_PK_SWIZZLE
+    int i0, j0;
+    {
+        constexpr int SW = 16;
+        const int t = blockIdx.x, band = t / (SW * a.tiles_x), ty0 = band * SW;
+        const int h = min(SW, a.tiles_y - ty0), rem = t - band * SW * a.tiles_x;
+        i0 = (rem / h) * kTileX;
+        j0 = (ty0 + rem % h) * kTileY;
+    }
+#else
     const int i0 = (blockIdx.x % a.tiles_x) * kTileX, j0 = (blockIdx.x / a.tiles_x) * kTileY;
+#endif
     const int ci = i0 + (lane & 15), cj = j0 + warp * 2 + (lane >> 4);
     const float ip = (float)ci - a.cx, jp = (float)cj - a.cy, kp0 = (float)k0 - a.cz;
 
@@ -434,12 +447,19 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
         vcnt = a.view_begin + (int)(((long long)a.view_count * (blockIdx.z + 1)) / a.splits) - vbeg;
     }
     const int ngroups = NV * vcnt;
+#if IFDK_PK_ROTATE
+    const long long lin = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    const int rot = vcnt > 0 ? (int)((lin * vcnt / a.resident) % vcnt) : 0;
+#else
+    const int rot = 0;
+#endif
     // Lane 0 of warp 0: window of group t (own view's footprint of the tile),
     // its terms and the TMA box into stage t % S.
     auto issue = [&](int t) {
         const int st = t % S;
         const uint32_t sg = s0 + kPkStage0 + (uint32_t)st * a.stage_bytes;
-        const int s = vbeg + (NV == 2 ? (t >> 1) : t);    // view 0 of the box
+        const int qv = (NV == 2 ? (t >> 1) : t) + rot;
+        const int s = vbeg + (qv >= vcnt ? qv - vcnt : qv);    // view 0 of the box
         const int own = s + (NV == 2 ? (t & 1) * a.pair_view_off : 0);
         const float4 *tp = reinterpret_cast<const float4 *>(a.terms + own);
         const float4 t0 = __ldg(tp), t1 = __ldg(tp + 1);
@@ -764,9 +784,11 @@ int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_beg
     a.status = p->d_status;
     a.wait_ns = p->wait_ns;
     a.abort_group = p->test_abort_group;
+    a.resident = p->n_sm * pk_blocks(NV);
     a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
     a.ny_cols = NV == 2 ? g.ny / 2 : g.ny;
     a.tiles_x = (g.nx + kTileX - 1) / kTileX;
+    a.tiles_y = (a.ny_cols + kTileY - 1) / kTileY;
     a.view_begin = s_begin;
     a.view_count = s_count;
     a.q_view0 = q_view0;
