@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-view-pairing", action="store_true",
                     help="back-project every view singly (no half-turn view pairs)")
+    ap.add_argument("--pairing", type=int, default=2, choices=[1, 2],
+                    help="1: half-turn view pairs; 2: quarter-turn quads where they apply (FP16), pairs elsewhere")
     ap.add_argument("--view-split", type=int, default=0,
                     help="cap on the view split of small volumes (0 automatic, 1 off)")
     ap.add_argument("--standard", action="store_true",
@@ -322,7 +324,9 @@ class Arm:
     def __init__(self, plan, batches, tdt, dev, standard):
         from paper_1909_02724_gb300.api import BatchFdk
         g = plan.geom
-        self.bf = BatchFdk(plan, batches, dtype=tdt, device=dev, packed=not standard)
+        # quarter-turn quads where the plan serves this storage type with them
+        group = 4 if (not standard and plan.packed_info(tdt)["path"] == 4) else 2
+        self.bf = BatchFdk(plan, batches, dtype=tdt, device=dev, packed=not standard, group=group)
         self.vol = torch_empty_vol(g, dev)
 
     def step(self, E, k, ev=None):
@@ -333,7 +337,7 @@ class Arm:
 
     def updates(self, k) -> int:
         g = self.bf.plan.geom
-        return g.nx * g.ny * g.nz * 2 * self.bf.views(k % self.bf.batches)[1]
+        return g.nx * g.ny * g.nz * self.bf.group * self.bf.views(k % self.bf.batches)[1]
 
     def finish(self, E, k_next):
         """Runs the batches left in the current reconstruction (untimed), so that the
@@ -375,7 +379,7 @@ def run_ours(args):
     tdt = dts[args.dtype]
     dev = torch.device("cuda", local)
     plan = B.Plan(g)
-    plan.set_view_pairing(not args.no_view_pairing)
+    plan.set_view_pairing(0 if args.no_view_pairing else args.pairing)
     plan.set_view_split(args.view_split)
     packed = not args.standard and plan.has_packed(tdt)
     info = plan.packed_info(tdt) if packed else plan.info(tdt)
@@ -428,7 +432,7 @@ def run_ours(args):
     ws_min, ws_pref = B.ifdk_filter_workspace_size(plan.handle, terms)
     cap = ws_pref // (ws_min // 128)
     half_rows = arm.bf.n * g.nv
-    bp_launches = 1 if (packed and info["path"] == 2) else 2
+    bp_launches = 1 if (packed and info["path"] in (2, 4)) else 2
     splits = plan.view_split(tdt) if packed else 1
     per_step = 2 * 2 * -(-half_rows // cap) + (1 if packed else 0) + bp_launches * (2 if splits > 1 else 1)
     launches = per_step * args.steps
@@ -456,7 +460,8 @@ def run_ours(args):
         E_host = torch.empty(E.shape, dtype=torch.float32, pin_memory=True)
         E_host.copy_(E)
         vol_host = torch.empty(arm.vol.shape, dtype=torch.float32, pin_memory=True)
-        E_b = [torch.empty((2 * arm.bf.n, g.nv, g.nu), dtype=torch.float32, device=dev) for _ in range(2)]
+        E_b = [torch.empty((arm.bf.group * arm.bf.n, g.nv, g.nu), dtype=torch.float32, device=dev)
+               for _ in range(2)]
         vol2 = [arm.vol, torch.empty_like(arm.vol)]
         e_steps = max(batches, min(args.steps, 2 * batches))
         batch_host_pipeline(arm.bf, E_host, vol_host, E_b, vol2, batches)          # warm
@@ -467,7 +472,7 @@ def run_ours(args):
         batch_host_pipeline(arm.bf, E_host, vol_host, E_b, vol2, e_steps)
         e_s = max_over_ranks(time.perf_counter() - a, device=dev)
         e_upd = sum(arm.updates(k) for k in range(e_steps))
-        h2d = sum(2 * arm.bf.views(k % batches)[1] for k in range(e_steps)) * g.nv * g.nu * 4
+        h2d = sum(arm.bf.group * arm.bf.views(k % batches)[1] for k in range(e_steps)) * g.nv * g.nu * 4
         d2h = (e_steps // batches) * arm.vol.numel() * 4
         e2e = {"value": world * e_upd / e_s / 2 ** 30, "unit": UNIT,
                "h2d_bytes_per_step": h2d // e_steps, "d2h_bytes_per_step": d2h // e_steps,
@@ -493,7 +498,7 @@ def run_ours(args):
     nominal = n_sm * 128 * f_max / FP32_OPS_PER_UPDATE / 2 ** 30
     if packed:
         kname, kfile = "bp_packed_kernel", "ifdk_bp_packed.cu"
-        prof = f"bp_packed_{args.workload}_{args.dtype}" + ("" if info["path"] == 2 else "_single")
+        prof = f"bp_packed_{args.workload}_{args.dtype}" + {2: "", 4: "_quads"}.get(info["path"], "_single")
     else:
         kname = "bp_pairs_fold_kernel" if info["path"] == 1 else "bp_general_kernel"
         kfile, prof = "ifdk_bp.cu", f"bp_fold_{args.workload}"
@@ -528,6 +533,7 @@ def run_ours(args):
     if not args.no_cpu and world == 1:
         acc = oracle_accuracy(w, E, accuracy_sample(g))
 
+    main_bf_group, main_bf_n = arm.bf.group, arm.bf.n
     storage_arms = {}
     if not args.no_arms and world == 1:
         others = [d for d in ("f16", "bf16", "f32") if d != args.dtype]
@@ -554,12 +560,15 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": workload_desc(w), "storage": args.dtype, "accumulate": "f32",
-                       "step": f"one batch: filter + pack + back-project {2 * arm_views(plan, batches)} views "
-                               f"({arm_views(plan, batches)} half-turn pairs) of the {g.np}-view scan; "
+                       "step": f"one batch: filter + pack + back-project {main_bf_group * main_bf_n} views "
+                               f"({main_bf_n} {'half-turn pairs' if main_bf_group == 2 else 'quarter-turn quads'}) "
+                               f"of the "
+                               f"{g.np}-view scan; "
                                f"{batches} steps = one reconstruction (volume zeroed at its first)",
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (E, Q, Qp and the volume each >= 256 MiB)",
-                       "bp_path": ("packed views" + (", half-turn view pairs" if info["path"] == 2 else ""))
+                       "bp_path": ("packed views" + {2: ", half-turn view pairs", 4: ", quarter-turn view quads"}
+                                   .get(info["path"], ""))
                        if packed else "filtered views as stored",
                        "bp_launch": info, "view_split": splits},
             "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roofline,
@@ -571,10 +580,6 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
-
-
-def arm_views(plan, batches) -> int:
-    return -(-(plan.geom.np // 2) // batches)
 
 
 def run_arm(plan, batches, tdt, dev, standard, E, vol_ref, acc, roofline_of, key) -> dict:
@@ -595,6 +600,7 @@ def run_arm(plan, batches, tdt, dev, standard, E, vol_ref, acc, roofline_of, key
     upd = sum(arm.updates(k) for k in range(batches))
     bp = float(np.mean([arm.updates(k) / (a.elapsed_time(b) * 1e-3) / 2 ** 30 for k, (a, b) in enumerate(ev)]))
     out = {"step_gups": upd / (t0.elapsed_time(t1) * 1e-3) / 2 ** 30, "bp_gups": bp,
+           "bp_path": {2: "half-turn view pairs", 4: "quarter-turn view quads"}.get(arm.bf.group),
            "roofline": {k2: v for k2, v in roofline_of(bp, key).items()
                         if k2 in ("frac", "peak_path", "frac_path", "frac_nominal_128lane")},
            "rel_l2_vs_main_volume": rel_l2_chunked(arm.vol, vol_ref),

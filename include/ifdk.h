@@ -259,7 +259,18 @@ int ifdk_backproject_packed(ifdk_plan p, const void *Qp, int q_dtype, int view_b
    kind of rotational symmetry, after Zhao et al., and leaves it out because
    its pipeline receives views in scan order.)  Views of a call whose partner
    is outside the call's view range are back-projected singly.
-   enable = 0 turns pairing off for this plan, 1 back on. */
+   Quarter-turn view quads (enable = 2): when, in addition, view s + np/4 is
+   view s turned by exactly pi/2 (np a multiple of 4) and the column grid is
+   square (nx = ny, even, dx = dy), voxel (X, Y, Z) in view s and voxel
+   (Y, -X, Z) in view s + np/4 share (u, v, z), i.e. column (i, j) and
+   column (nx-1-j, i).  A thread then owns a column of one quadrant and its
+   three images, and each evaluation of the coordinates serves eight voxels
+   of the four views s, s + np/4, s + np/2, s + 3np/4 (the symmetry of Zhao
+   et al. that Sec. 3.2 cites).  Quads serve a call over the whole scan
+   (ifdk_backproject_packed and its pair-range form) and
+   ifdk_backproject_packed_quads; other view ranges use pairs.
+   enable = 0 turns pairing off for this plan, 1 selects half-turn pairs
+   (the default), 2 quarter-turn quads where they apply (pairs elsewhere). */
 int ifdk_set_view_pairing(ifdk_plan p, int enable);
 
 /* ifdk_backproject_packed for the mirror pairs k in [pair_begin, pair_begin +
@@ -291,9 +302,20 @@ int ifdk_backproject_packed_pairs(ifdk_plan p, const void *Qp, int q_dtype, int 
 int ifdk_backproject_packed_batch(ifdk_plan p, const void *Qpb, int q_dtype, int view_begin, int view_count,
                                   float *vol, void *stream);
 
+/* ifdk_backproject_packed_batch for quarter-turn view quads: Qpq holds
+   4 view_count packed views, views [view_begin, view_begin + view_count) and
+   then the same range shifted by np/4, np/2 and 3np/4 (ifdk_pack_views
+   layout), all added into vol (device FP32 [nx][ny][nz], ACCUMULATED into).
+   With quads on and available (ifdk_set_view_pairing mode 2) one launch
+   serves them; otherwise half-turn pairs, or single views.  np must be a
+   multiple of 4 and view_begin + view_count <= np/4 (else
+   IFDK_ERR_INVALID).  Alignment and other errors as ifdk_backproject_packed. */
+int ifdk_backproject_packed_quads(ifdk_plan p, const void *Qpq, int q_dtype, int view_begin, int view_count,
+                                  float *vol, void *stream);
+
 /* Describes a full-range ifdk_backproject_packed launch with q_dtype:
-   info[0] = path (2 = half-turn view pairs, 1 = single views, 0 = packed
-   path not available), info[1] = TMA box width (elements), info[2] = box
+   info[0] = path (4 = quarter-turn view quads, 2 = half-turn view pairs,
+   1 = single views, 0 = packed path not available), info[1] = TMA box width (elements), info[2] = box
    height (rows), info[3] = z pairs per thread, info[4] = TMA stages,
    info[5] = dynamic shared memory bytes per block, info[6] = blocks in the
    grid, info[7] = window width (pixels), info[8] = u alignment of the box
@@ -302,8 +324,8 @@ int ifdk_backproject_packed_batch(ifdk_plan p, const void *Qpb, int q_dtype, int
 int ifdk_backproject_packed_info(ifdk_plan p, int q_dtype, int64_t info[12]);
 
 /* Host-only query (no device needed): ifdk_backproject_packed_info for this
-   geometry and q_dtype with half-turn pairing on (view_pairing = 1) or off
-   (0).  Returns the geometry's validation status. */
+   geometry and q_dtype with view pairing mode view_pairing (0, 1 or 2, as
+   ifdk_set_view_pairing).  Returns the geometry's validation status. */
 int ifdk_query_packed(const ifdk_geometry *g, int q_dtype, int view_pairing, int64_t info[12]);
 
 /* Back-projection of filtered views streamed from host memory (the paper's

@@ -110,35 +110,40 @@ def fdk_host_pipeline(plan: Plan, E_host: torch.Tensor, vol_host: torch.Tensor, 
 
 
 class BatchFdk:
-    """FDK of a scan in batches of half-turn view pairs, the way the paper's
-    pipeline (Sec. 4) filters and back-projects projections in batches as they
-    arrive: batch b holds views [b n, b n + n) and their partners
-    [np/2 + b n, np/2 + b n + n), n = np / (2 batches) (the last batch takes the
-    remainder).  One batch is ifdk_filter_views on each half,
-    ifdk_pack_views on the 2 n filtered views and
-    ifdk_backproject_packed_batch into the accumulating volume (or, without
-    packed views, ifdk_backproject_views on each half).  The batch buffers
-    (filtered and packed views of one batch) are made here, once."""
+    """FDK of a scan in batches of half-turn view pairs (group = 2) or
+    quarter-turn view quads (group = 4), the way the paper's pipeline (Sec. 4)
+    filters and back-projects projections in batches as they arrive: batch b
+    holds views [b n, b n + n) and the same range shifted by np / group, ...,
+    (group - 1) np / group, n = np / (group batches) (the last batch takes the
+    remainder).  One batch is ifdk_filter_views on each part, ifdk_pack_views
+    on the group n filtered views and ifdk_backproject_packed_batch (pairs) or
+    ifdk_backproject_packed_quads (quads; the plan's view pairing mode decides
+    whether one quad launch or pair launches serve them) into the accumulating
+    volume (or, without packed views, ifdk_backproject_views on each part).
+    The batch buffers (filtered and packed views of one batch) are made here,
+    once."""
 
     def __init__(self, plan: Plan, batches: int, dtype=torch.float32, split_terms: int | None = None,
-                 device=None, packed: bool = True):
+                 device=None, packed: bool = True, group: int = 2):
         g = plan.geom
-        if g.np % 2 != 0 or not 1 <= batches <= g.np // 2:
-            raise ValueError("batches of half-turn pairs need an even view count and 1 <= batches <= np / 2")
+        if group not in (2, 4) or g.np % group != 0 or not 1 <= batches <= g.np // group:
+            raise ValueError("batches of view groups need group 2 or 4 dividing np and 1 <= batches <= np / group")
         dev = torch.device("cuda") if device is None else torch.device(device)
         self.plan, self.batches, self.dtype, self.split_terms = plan, batches, dtype, split_terms
-        self.half = g.np // 2
-        self.n = -(-self.half // batches)
+        self.group = group
+        self.part = g.np // group                     # view offset between the parts of a batch
+        self.half = self.part                         # (the name used by pairs)
+        self.n = -(-self.part // batches)
         self.packed = packed and plan.has_packed(dtype)
-        self.Q = torch.empty((2 * self.n, g.nv, g.nu), dtype=dtype, device=dev)
-        self.Qp = (torch.empty((2 * self.n,) + plan.packed_shape(dtype)[1:], dtype=dtype, device=dev)
+        self.Q = torch.empty((group * self.n, g.nv, g.nu), dtype=dtype, device=dev)
+        self.Qp = (torch.empty((group * self.n,) + plan.packed_shape(dtype)[1:], dtype=dtype, device=dev)
                    if self.packed else None)
 
     def views(self, b: int) -> tuple[int, int]:
-        """(first view, view count) of the first half of batch b; the second half is
-        the same range shifted by np / 2."""
+        """(first view, view count) of the first part of batch b; the other parts are
+        the same range shifted by k np / group."""
         s0 = b * self.n
-        return s0, max(0, min(self.n, self.half - s0))
+        return s0, max(0, min(self.n, self.part - s0))
 
     def step(self, E: torch.Tensor, vol: torch.Tensor, b: int, stream=None, ev_bp=None) -> None:
         """Batch b of the scan E (float32 CUDA [np][nv][nu], or a buffer holding just this
@@ -148,25 +153,28 @@ class BatchFdk:
         s0, n = self.views(b)
         if n == 0:
             return
-        if E.shape[0] == g.np:
-            Ea, Eb = E[s0:s0 + n], E[self.half + s0:self.half + s0 + n]
-        else:
-            Ea, Eb = E[:n], E[n:2 * n]
-        Qa, Qb = self.Q[:n], self.Q[n:2 * n]
-        self.plan.filter_views(Ea, Qa, view_begin=s0, split_terms=self.split_terms, stream=stream)
-        self.plan.filter_views(Eb, Qb, view_begin=self.half + s0, split_terms=self.split_terms, stream=stream)
+        K = self.group
+        for k in range(K):
+            v0 = s0 + k * self.part
+            Ek = E[v0:v0 + n] if E.shape[0] == g.np else E[k * n:(k + 1) * n]
+            self.plan.filter_views(Ek, self.Q[k * n:(k + 1) * n], view_begin=v0, split_terms=self.split_terms,
+                                   stream=stream)
         s = torch.cuda.current_stream() if stream is None else stream
         if self.packed:
-            Qpb = self.Qp[:2 * n]
-            self.plan.pack(self.Q[:2 * n], Qpb, stream=stream)
+            Qpb = self.Qp[:K * n]
+            self.plan.pack(self.Q[:K * n], Qpb, stream=stream)
             if ev_bp is not None:
                 ev_bp[0].record(s)
-            self.plan.backproject_packed_batch(Qpb, s0, n, vol, stream=stream)
+            if K == 2:
+                self.plan.backproject_packed_batch(Qpb, s0, n, vol, stream=stream)
+            else:
+                self.plan.backproject_packed_quads(Qpb, s0, n, vol, stream=stream)
         else:
             if ev_bp is not None:
                 ev_bp[0].record(s)
-            self.plan.backproject_views(Qa, vol, view_begin=s0, stream=stream)
-            self.plan.backproject_views(Qb, vol, view_begin=self.half + s0, stream=stream)
+            for k in range(K):
+                self.plan.backproject_views(self.Q[k * n:(k + 1) * n], vol, view_begin=s0 + k * self.part,
+                                            stream=stream)
         if ev_bp is not None:
             ev_bp[1].record(s)
 
@@ -203,8 +211,9 @@ def batch_host_pipeline(bf: BatchFdk, E_host: torch.Tensor, vol_host: torch.Tens
         with torch.cuda.stream(s_in):
             if k >= 2:
                 s_in.wait_event(used[e])                   # step k-2's filters have read E_dev[e]
-            E_dev[e][:n].copy_(E_host[s0:s0 + n], non_blocking=True)
-            E_dev[e][n:2 * n].copy_(E_host[bf.half + s0:bf.half + s0 + n], non_blocking=True)
+            for q in range(bf.group):
+                v0 = s0 + q * bf.part
+                E_dev[e][q * n:(q + 1) * n].copy_(E_host[v0:v0 + n], non_blocking=True)
             copied[e].record(s_in)
         s_c.wait_event(copied[e])
         if b == 0:

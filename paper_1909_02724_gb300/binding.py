@@ -35,7 +35,8 @@ EXPORTS = ("ifdk_create", "ifdk_destroy", "ifdk_filter", "ifdk_filter_workspace_
            "ifdk_backproject_packed_info", "ifdk_query_packed", "ifdk_volume_slices",
            "ifdk_set_view_split", "ifdk_view_split", "ifdk_filter_max", "ifdk_set_short_scan",
            "ifdk_backproject_packed_pairs", "ifdk_filter_views", "ifdk_backproject_packed_batch",
-           "ifdk_arith_rate", "ifdk_iter_ratio", "ifdk_iter_update", "ifdk_set_test_abort")
+           "ifdk_arith_rate", "ifdk_iter_ratio", "ifdk_iter_update", "ifdk_set_test_abort",
+           "ifdk_backproject_packed_quads")
 
 
 class IfdkError(RuntimeError):
@@ -106,6 +107,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.ifdk_view_split.argtypes = [vp, i32, ctypes.POINTER(i32)]
         lib.ifdk_filter_views.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp, ctypes.c_size_t, vp]
         lib.ifdk_backproject_packed_batch.argtypes = [vp, vp, i32, i32, i32, vp, vp]
+        lib.ifdk_backproject_packed_quads.argtypes = [vp, vp, i32, i32, i32, vp, vp]
         lib.ifdk_set_test_abort.argtypes = [vp, i32]
         lib.ifdk_iter_ratio.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp]
         lib.ifdk_iter_update.argtypes = [vp, i32, vp, vp, vp, ctypes.c_float, i32, vp]
@@ -297,6 +299,14 @@ def ifdk_iter_update(plan: int, method: int, x, U, C, lam: float, nonneg: bool, 
                                            int(bool(nonneg)), _stream(stream)), "ifdk_iter_update")
 
 
+def ifdk_backproject_packed_quads(plan: int, Qpq, q_dtype: int, view_begin: int, view_count: int, vol,
+                                  stream=None) -> None:
+    """Qpq: packed views [view_begin, +view_count) and the same shifted by np/4, np/2, 3np/4."""
+    _check(load_library().ifdk_backproject_packed_quads(plan, _addr(Qpq), int(q_dtype), int(view_begin),
+                                                        int(view_count), _addr(vol), _stream(stream)),
+           "ifdk_backproject_packed_quads")
+
+
 def ifdk_arith_rate(kind: int, blocks: int, iters: int, sink, clocks, stream=None) -> tuple[int, int]:
     """Launches the arithmetic rate probe; returns (instructions per thread, lanes per instruction)."""
     out = (ctypes.c_int64 * 2)()
@@ -312,8 +322,17 @@ def pair_slab_depth(nz: int, pair_begin: int, pair_count: int) -> int:
     return 2 * pair_count - (1 if nz % 2 and pair_begin + pair_count == npairs and pair_count > 0 else 0)
 
 
-def ifdk_set_view_pairing(plan: int, enable: bool) -> None:
-    _check(load_library().ifdk_set_view_pairing(plan, 1 if enable else 0), "ifdk_set_view_pairing")
+def _pairing_mode(mode) -> int:
+    """False / True / 0 / 1 / 2 -> the C mode (0 off, 1 half-turn pairs, 2 quarter-turn quads)."""
+    if isinstance(mode, bool):
+        return 1 if mode else 0
+    if mode not in (0, 1, 2):
+        raise ValueError("view pairing mode must be 0, 1 or 2")
+    return int(mode)
+
+
+def ifdk_set_view_pairing(plan: int, enable) -> None:
+    _check(load_library().ifdk_set_view_pairing(plan, _pairing_mode(enable)), "ifdk_set_view_pairing")
 
 
 _PACKED_KEYS = ("path", "box_w", "box_h", "z_per_thread", "stages", "smem_bytes", "blocks", "fold_w", "align",
@@ -326,11 +345,12 @@ def ifdk_backproject_packed_info(plan: int, q_dtype: int) -> dict:
     return dict(zip(_PACKED_KEYS, (int(v) for v in arr)))
 
 
-def ifdk_query_packed(geom: Geometry, q_dtype: int, view_pairing: bool = True) -> dict:
-    """Host-only: the packed launch ifdk_backproject_packed would choose."""
+def ifdk_query_packed(geom: Geometry, q_dtype: int, view_pairing=True) -> dict:
+    """Host-only: the packed launch ifdk_backproject_packed would choose (view_pairing:
+    False / True, or the mode 0, 1, 2 of ifdk_set_view_pairing)."""
     h = _GeomHolder(geom)
     arr = (ctypes.c_int64 * 12)()
-    _check(load_library().ifdk_query_packed(ctypes.byref(h.c), int(q_dtype), 1 if view_pairing else 0, arr),
+    _check(load_library().ifdk_query_packed(ctypes.byref(h.c), int(q_dtype), _pairing_mode(view_pairing), arr),
            "ifdk_query_packed")
     return dict(zip(_PACKED_KEYS, (int(v) for v in arr)))
 
@@ -623,9 +643,24 @@ class Plan:
         ifdk_backproject_packed_batch(self.handle, Qpb, dtype_code(Qpb.dtype), view_begin, view_count, vol, stream)
         return vol
 
-    def set_view_pairing(self, enable: bool) -> None:
-        """Half-turn view pairing of the packed back-projection (on by default)."""
+    def set_view_pairing(self, enable) -> None:
+        """View pairing of the packed back-projection: False / 0 off, True / 1 half-turn pairs
+        (the default), 2 quarter-turn quads where they apply."""
         ifdk_set_view_pairing(self.handle, enable)
+
+    def backproject_packed_quads(self, Qpq, view_begin: int, view_count: int, vol=None, stream=None):
+        """ifdk_backproject_packed_quads: Qpq (4 view_count, rows, row_elems, 4) holds the packed views
+        [view_begin, +view_count) and the same range shifted by np/4, np/2 and 3np/4."""
+        import torch
+        g = self.geom
+        shape = (4 * view_count,) + self.packed_shape(Qpq.dtype)[1:]
+        if not Qpq.is_cuda or not Qpq.is_contiguous() or tuple(Qpq.shape) != shape:
+            raise ValueError(f"Qpq must be a contiguous CUDA tensor of shape {shape}")
+        if vol is None:
+            vol = torch.zeros((g.nx, g.ny, g.nz), dtype=torch.float32, device=Qpq.device)
+        self._check_vol(vol)
+        ifdk_backproject_packed_quads(self.handle, Qpq, dtype_code(Qpq.dtype), view_begin, view_count, vol, stream)
+        return vol
 
     def packed_info(self, dtype) -> dict:
         return ifdk_backproject_packed_info(self.handle, dtype_code(dtype))

@@ -29,11 +29,25 @@
 //     opposite column with view s.  So each pair of views is two view groups,
 //     and each evaluation of the coordinates, the row index and the row
 //     fraction serves four voxel updates;
+//   * quarter-turn view quads (NV = 4, FP16 storage): when view s + np/4 is
+//     view s turned by pi/2 and the column grid is square, column (i, j) in
+//     view s and column (nx-1-j, i) in view s + np/4 share (u, v, z).  A
+//     thread owns a column of one quadrant and its three images under the
+//     quarter turn; a view quad (s, s + np/4, s + np/2, s + 3np/4) is four
+//     view groups, and each evaluation of the coordinates serves eight voxel
+//     updates (the symmetry after Zhao et al. that Sec. 3.2 cites);
 //   * a view group's window (the tile's detector footprint in the group's
-//     own view, rows [v0, v0+H)) is one TMA box of the packed views s and
-//     s + P together (a 4-D tensor map whose second dimension steps from view
-//     s to view s + P), so the two views' elements of a row sit side by side;
-//     TMA's zero fill implements "taps outside the detector read 0";
+//     own view, rows [v0, v0+H)) is one TMA box of the NV packed views of
+//     the group's pair or quad together (a 4-D tensor map whose second
+//     dimension steps from view s to view s + np/NV), so the views' elements
+//     of a row sit side by side; TMA's zero fill implements "taps outside
+//     the detector read 0";
+//   * L2 locality: blocks take their column tiles in bands of 16 tile rows,
+//     and each block starts its cycle over the views at a view group fixed by
+//     its place in the launch order, so that the blocks resident at one time
+//     work on the same views of a compact patch of columns and share the
+//     windows in L2 (the views' order in a block's sum is fixed: the result
+//     is reproducible);
 //   * a ring of stages (one group each) paced by mbarriers: full = the box
 //     landed, empty = every warp finished the group.  At group t, warp
 //     t mod 8 refills the stage group t - 2 used with group t - 2 + stages
@@ -59,6 +73,7 @@ namespace ifdk {
 namespace {
 
 constexpr int kPkMargin = 1;   // window margin (pixels) on every side
+constexpr int kPkSwizzle = 16; // tile rows per band of the block order
 
 struct PkGeom {              // per stage: the group's window and terms (64 bytes)
     float A0, A1, A3, B2;    // own view's projection terms (Eq. 2, re-centred)
@@ -72,10 +87,11 @@ struct PkArgs {
     const ViewTerms *terms;
     unsigned int *status;
     unsigned long long wait_ns;
-    int nx, ny, nz, tiles_x, ny_cols;   // ny_cols: rows j the grid covers (ny, or ny / 2 with NV = 2)
+    int nx, ny, nz, tiles_x, ny_cols;   // ny_cols: rows j the grid covers (ny, or ny / 2 with NV = 2, 4)
+    int nx_cols;                        // columns i the grid covers (nx, or nx / 2 with NV = 4)
     int view_begin, view_count;         // NV = 1: views; NV = 2: pairs (s, s + P), s from view_begin
     int q_view0, q_pair_off;            // view s is packed view s - q_view0 (its partner + q_pair_off)
-    int pair_view_off;                  // P
+    int pair_view_off;                  // view offset between the box's slots: np / NV
     int box_h, stages, row0;            // row0: detector row of packed row 0
     float cx, cy, cz, uc, vc;
     float wscale, wunscale;             // power of two on the FDK weights (FP16: keeps W in range) and its inverse
@@ -291,12 +307,14 @@ __device__ __forceinline__ const unsigned char *chk_row(const unsigned char *e, 
 #define PK_ROW(ptr) Tap<T>::row((ptr), du2, duh)
 #endif
 
-template <typename T, int NV, int L, uint32_t ROWB, uint32_t HB, Reuse MODE>
-__device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], const unsigned char *sm,
-                                          uint32_t base, float sig, float vb, float2 du2, __half2 duh,
-                                          typename Tap<T>::Wt W0, typename Tap<T>::Wt W1 PK_CHK_PARAM)
+template <typename T, int NV, int L, uint32_t ROWB, uint32_t HB, Reuse MODE, int G>
+__device__ __forceinline__ void pair_loop(float2 (&acc)[NV][L], const unsigned char *sm, uint32_t base, float sig,
+                                          float vb, float2 du2, __half2 duh,
+                                          const typename Tap<T>::Wt (&W)[NV] PK_CHK_PARAM)
 {
     using R = typename Tap<T>::R;
+    // box slot n (view s + n np/NV) feeds column (n - G) mod NV of the thread (the
+    // loops over n are unrolled: every index below is a constant)
     R lo[NV], hi[NV];
     float dv;
     uint32_t tv = floor_frac(vb, dv);
@@ -306,8 +324,10 @@ __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], cons
         lo[n] = PK_ROW(e + n * HB);
         hi[n] = PK_ROW(e + ROWB + n * HB);
     }
-    a0[0] = Tap<T>::accum(a0[0], lo[0], hi[0], make_float2(dv, dv), __float2half2_rn(dv), W0);
-    if constexpr (NV == 2) a1[0] = Tap<T>::accum(a1[0], lo[1], hi[1], make_float2(dv, dv), __float2half2_rn(dv), W1);
+#pragma unroll
+    for (int n = 0; n < NV; ++n)
+        acc[(n + NV - G) % NV][0] =
+            Tap<T>::accum(acc[(n + NV - G) % NV][0], lo[n], hi[n], make_float2(dv, dv), __float2half2_rn(dv), W[n]);
 #pragma unroll
     for (int p = 1; p < L; ++p) {
         const uint32_t tn = floor_frac(fmaf((float)p, sig, vb), dv);
@@ -341,8 +361,9 @@ __device__ __forceinline__ void pair_loop(float2 (&a0)[L], float2 (&a1)[L], cons
                 hi[n] = hn;
             }
         }
-        a0[p] = Tap<T>::accum(a0[p], lo[0], hi[0], dv2, dvh, W0);
-        if constexpr (NV == 2) a1[p] = Tap<T>::accum(a1[p], lo[1], hi[1], dv2, dvh, W1);
+#pragma unroll
+        for (int n = 0; n < NV; ++n)
+            acc[(n + NV - G) % NV][p] = Tap<T>::accum(acc[(n + NV - G) % NV][p], lo[n], hi[n], dv2, dvh, W[n]);
     }
 }
 
@@ -410,19 +431,17 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
     const int S = a.stages;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // block coordinates: warp = 16 x 2 patch of columns, 8 warps per 16 x 16 tile
-#if IFDK_PK_SWIZZLE
+    // block coordinates: warp = 16 x 2 patch of columns, 8 warps per 16 x 16 tile.
+    // Tiles go in bands of kPkSwizzle tile rows, column by column within a band,
+    // so that the blocks resident at one time cover a compact patch of columns
+    // (a small detector footprint per view, shared in L2).
     int i0, j0;
     {
-        constexpr int SW = 16;
-        const int t = blockIdx.x, band = t / (SW * a.tiles_x), ty0 = band * SW;
-        const int h = min(SW, a.tiles_y - ty0), rem = t - band * SW * a.tiles_x;
+        const int t = blockIdx.x, band = t / (kPkSwizzle * a.tiles_x), ty0 = band * kPkSwizzle;
+        const int h = min(kPkSwizzle, a.tiles_y - ty0), rem = t - band * kPkSwizzle * a.tiles_x;
         i0 = (rem / h) * kTileX;
         j0 = (ty0 + rem % h) * kTileY;
     }
-#else
-    const int i0 = (blockIdx.x % a.tiles_x) * kTileX, j0 = (blockIdx.x / a.tiles_x) * kTileY;
-#endif
     const int ci = i0 + (lane & 15), cj = j0 + warp * 2 + (lane >> 4);
     const float ip = (float)ci - a.cx, jp = (float)cj - a.cy, kp0 = (float)k0 - a.cz;
 
@@ -447,24 +466,28 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
         vcnt = a.view_begin + (int)(((long long)a.view_count * (blockIdx.z + 1)) / a.splits) - vbeg;
     }
     const int ngroups = NV * vcnt;
-#if IFDK_PK_ROTATE
+    // The block starts its view cycle at view group rot, a fixed function of its
+    // place in the launch order: blocks start about a.resident at a time, so a
+    // block starting while the others are part-way through the views joins
+    // them at the views they are on.  The blocks resident together then read
+    // the same views' windows at the same time (in L2) instead of each its
+    // own.  The order of the views in a block's sum depends only on the
+    // block, so the result is reproducible.
     const long long lin = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     const int rot = vcnt > 0 ? (int)((lin * vcnt / a.resident) % vcnt) : 0;
-#else
-    const int rot = 0;
-#endif
     // Lane 0 of warp 0: window of group t (own view's footprint of the tile),
     // its terms and the TMA box into stage t % S.
     auto issue = [&](int t) {
         const int st = t % S;
         const uint32_t sg = s0 + kPkStage0 + (uint32_t)st * a.stage_bytes;
-        const int qv = (NV == 2 ? (t >> 1) : t) + rot;
-        const int s = vbeg + (qv >= vcnt ? qv - vcnt : qv);    // view 0 of the box
-        const int own = s + (NV == 2 ? (t & 1) * a.pair_view_off : 0);
+        const int qv = t / NV + rot;
+        const int s = vbeg + (qv >= vcnt ? qv - vcnt : qv);    // view of the box's slot 0
+        const int own = s + (t % NV) * a.pair_view_off;          // the group's own view: slot t mod NV
         const float4 *tp = reinterpret_cast<const float4 *>(a.terms + own);
         const float4 t0 = __ldg(tp), t1 = __ldg(tp + 1);
-        const float w0 = __ldg(&a.terms[s].w) * a.wscale;
-        const float w1 = NV == 2 ? __ldg(&a.terms[s + a.pair_view_off].w) * a.wscale : 0.0f;
+        float w[4] = {0.0f, 0.0f, 0.0f, 0.0f};                  // FDK weights of the slots' views
+#pragma unroll
+        for (int n = 0; n < NV; ++n) w[n] = __ldg(&a.terms[s + n * a.pair_view_off].w) * a.wscale;
         // t0 = (A0, A1, A3, B2), t1 = (B3, C0, C1, C3)
         const float ia = (float)i0 - a.cx, ib = ia + (kTileX - 1);
         const float ja = (float)j0 - a.cy, jb = ja + (kTileY - 1);
@@ -486,13 +509,14 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
         const int v0 = (int)floorf(a.vc + v_lo) - kPkMargin;
         sts_f32x4(sg, t0);
         sts_f32x4(sg + 16, t1);
-        sts_f32x4(sg + 32, make_float4(w0, a.uc - (float)u0a, a.vc - (float)v0, w1));
+        sts_f32x4(sg + 32, make_float4(w[0], a.uc - (float)u0a, a.vc - (float)v0, w[1]));
+        if constexpr (NV == 4) sts_f32x4(sg + 48, make_float4(w[2], w[3], 0.0f, 0.0f));
         const uint32_t bar = s0 + kPkFull + 8u * st;
         sts_u32(s0 + kPkLast + 4u * st, (uint32_t)t);
         fence_proxy_async_shared();
         mbar_arrive_expect_tx(bar, a.box_tx_bytes);
         const int q = s - a.q_view0;
-        if constexpr (NV == 2)
+        if constexpr (NV >= 2)   // the box spans the NV slots (second dimension)
             tma_load_4d(sg + kPkBox, &tmap, 4 * (u0a + 1), 0, v0 - a.row0, q, bar);
         else
             tma_load_3d(sg + kPkBox, &tmap, 4 * (u0a + 1), v0 - a.row0, q, bar);
@@ -509,12 +533,14 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
 #pragma unroll
         for (int p = 0; p < L; ++p) acc[n][p] = make_float2(0.0f, 0.0f);
 
-    // One view group t: wait for its box, form the column terms, run the z-run.
-    // SWAP (the second group of a half-turn pair): the box's view 0 (view s)
-    // feeds the opposite column and view 1 (view s + P) this thread's column.
+    // One view group t = NV q + G: wait for its box, form the column terms of
+    // the group's own view (the box's slot G) at this thread's column, run the
+    // z-run.  Rotational symmetry: the same coordinates belong to the thread's
+    // column m in the view of slot (G + m) mod NV, so slot n feeds column
+    // (n - G) mod NV.
     bool ok = true;
-    auto group = [&](int t, auto swap_tag) {
-        constexpr bool SWAP = decltype(swap_tag)::value;
+    auto group = [&](int t, auto g_tag) {
+        constexpr int G = decltype(g_tag)::value;
         const int st = t % S;
         const uint32_t parity = (uint32_t)(t / S) & 1u;
         // refill the stage group t - 2 used (every warp finished it by now, or soon)
@@ -533,6 +559,7 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
         const uint32_t sg = kPkStage0 + (uint32_t)st * a.stage_bytes;
         const float4 *gp = reinterpret_cast<const float4 *>(sm + sg);
         const float4 t0 = gp[0], t1 = gp[1], t2 = gp[2];
+        const float4 t3 = NV == 4 ? gp[3] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         // Theorems 2 and 3: z, u and W_dis do not depend on k
         const float z = fmaf(t1.y, ip, fmaf(t1.z, jp, t1.w));
         const float f = rcp_nr(z);
@@ -540,7 +567,10 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
         float du;
         const uint32_t tu = floor_frac(fmaf(x, f, t2.y), du);
         const float ff = f * f;
-        const typename Tap<T>::Wt W0 = Tap<T>::weight(t2.x * ff), W1 = Tap<T>::weight(t2.w * ff);
+        const float wsl[4] = {t2.x, t2.w, t3.x, t3.y};
+        typename Tap<T>::Wt W[NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) W[n] = Tap<T>::weight(wsl[n] * ff);
         const float sig = t0.w * f;
         const float vb = fmaf(sig, kp0, fmaf(t1.x, f, t2.z));
         // element (n, cu) at offset base + bits(t_v) * ROWB (mod 2^32): n = bits(t_v) - bias,
@@ -548,8 +578,6 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
         const uint32_t base = sg + kPkBox + (tu - kFloorBias) * ES - kFloorBias * ROWB;
         const float2 du2 = make_float2(du, du);
         const __half2 duh = __float2half2_rn(du);
-        float2(&c0)[L] = SWAP ? acc[NV - 1] : acc[0];
-        float2(&c1)[L] = SWAP ? acc[0] : acc[NV - 1];
         // sig < 1 - 2^-10 keeps fp32 rounding of v_{p+1} - v_p below one row; the
         // plan keeps every sig below 1.9 (two rows at most)
         // (FP32 taps keep the reuse across two-row steps; 16-bit taps load both rows,
@@ -559,19 +587,20 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
         const ChkBox chk{sm + sg + kPkBox, sm + sg + kPkBox + a.box_tx_bytes, a.status};
 #endif
         if (__all_sync(0xffffffffu, sig < 0.9990234375f))
-            pair_loop<T, NV, L, ROWB, HB, Reuse::STEP1>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1 PK_CHK_ARG);
+            pair_loop<T, NV, L, ROWB, HB, Reuse::STEP1, G>(acc, sm, base, sig, vb, du2, duh, W PK_CHK_ARG);
         else
-            pair_loop<T, NV, L, ROWB, HB, WIDE>(c0, c1, sm, base, sig, vb, du2, duh, W0, W1 PK_CHK_ARG);
+            pair_loop<T, NV, L, ROWB, HB, WIDE, G>(acc, sm, base, sig, vb, du2, duh, W PK_CHK_ARG);
         __syncwarp();
         if (lane == 0) mbar_arrive(s0 + kPkEmpty + 8u * st);
     };
-    if constexpr (NV == 2) {
-        for (int t = 0; ok && t < ngroups; t += 2) {
-            group(t, std::false_type{});
-            if (ok) group(t + 1, std::true_type{});
+    for (int t = 0; ok && t < ngroups; t += NV) {
+        group(t, std::integral_constant<int, 0>{});
+        if constexpr (NV >= 2)
+            if (ok) group(t + 1, std::integral_constant<int, 1>{});
+        if constexpr (NV == 4) {
+            if (ok) group(t + 2, std::integral_constant<int, 2>{});
+            if (ok) group(t + 3, std::integral_constant<int, 3>{});
         }
-    } else {
-        for (int t = 0; ok && t < ngroups; ++t) group(t, std::false_type{});
     }
     if (!ok) {
         // record the timeout; every exiting warp waits (bounded) for the last box
@@ -592,17 +621,30 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
 #pragma unroll
             for (int p = 0; p < L; ++p) acc[n][p] = make_float2(acc[n][p].x * a.wunscale, acc[n][p].y * a.wunscale);
     }
-    if (ci < a.nx && cj < a.ny_cols) {
-        if constexpr (!SPLIT) {
-            write_run<L, true, false>(a, a.vol, k0, ci, cj, acc[0]);
-            if constexpr (NV == 2) write_run<L, true, false>(a, a.vol, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
-        } else if (a.part != nullptr) {
-            float *dst = a.part + blockIdx.z * a.part_stride;
-            write_run<L, false, true>(a, dst, k0, ci, cj, acc[0]);
-            if constexpr (NV == 2) write_run<L, false, true>(a, dst, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
-        } else {
-            write_run<L, true, true>(a, a.vol, k0, ci, cj, acc[0]);
-            if constexpr (NV == 2) write_run<L, true, true>(a, a.vol, k0, a.nx - 1 - ci, a.ny - 1 - cj, acc[NV - 1]);
+    if (ci < a.nx_cols && cj < a.ny_cols) {
+        // the thread's columns: (ci, cj) and its images under the scan's turn by
+        // 2 pi / NV (a quarter turn maps (i, j) to (nx-1-j, i); nx = ny for NV = 4)
+        int cx[NV], cy[NV];
+        cx[0] = ci;
+        cy[0] = cj;
+        if constexpr (NV == 2) {
+            cx[1] = a.nx - 1 - ci;
+            cy[1] = a.ny - 1 - cj;
+        }
+        if constexpr (NV == 4) {
+            cx[1] = a.nx - 1 - cj; cy[1] = ci;
+            cx[2] = a.nx - 1 - ci; cy[2] = a.ny - 1 - cj;
+            cx[3] = cj;            cy[3] = a.ny - 1 - ci;
+        }
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            if constexpr (!SPLIT) {
+                write_run<L, true, false>(a, a.vol, k0, cx[m], cy[m], acc[m]);
+            } else if (a.part != nullptr) {
+                write_run<L, false, true>(a, a.part + blockIdx.z * a.part_stride, k0, cx[m], cy[m], acc[m]);
+            } else {
+                write_run<L, true, true>(a, a.vol, k0, cx[m], cy[m], acc[m]);
+            }
         }
     }
 }
@@ -709,13 +751,18 @@ PkLaunch size_packed(const ifdk_plan_s *p, int q_dtype, int nv)
     b.nv = nv;
     const int es = (int)dtype_size(q_dtype);
     b.align = q_dtype == IFDK_F32 ? 1 : 2;
-    const int ny_cols = nv == 2 ? g.ny / 2 : g.ny;
-    const int tiles_x = (g.nx + kTileX - 1) / kTileX, tiles_y = (ny_cols + kTileY - 1) / kTileY;
+    const int ny_cols = nv >= 2 ? g.ny / 2 : g.ny, nx_cols = nv == 4 ? g.nx / 2 : g.nx;
+    const int tiles_x = (nx_cols + kTileX - 1) / kTileX, tiles_y = (ny_cols + kTileY - 1) / kTileY;
     const int L = pk_pairs(nv, q_dtype), npairs = (g.nz + 1) / 2;
     b.grid_x = tiles_x * tiles_y;
     b.grid_y = pk_zblocks(npairs, L);
     if (!p->fold_ok) return b;
     if (nv == 2 && (!p->half_turn || g.ny % 2 != 0)) return b;
+    // a quarter turn maps the column grid onto itself: square grid, equal pitches, even size;
+    // quads are built for FP16 storage only (four columns' FP32 runs and four views' wider
+    // taps do not fit the registers of FP32 / BF16 taps without spilling)
+    if (nv == 4 && (!p->quarter_turn || g.nx != g.ny || g.nx % 2 != 0 || g.dx != g.dy || q_dtype != IFDK_F16))
+        return b;
     const double cx = (g.nx - 1) / 2.0, cy = (g.ny - 1) / 2.0, cz = (g.nz - 1) / 2.0;
     const double xa = cx * g.dx, xb = (tiles_x * kTileX - 1 - cx) * g.dx;
     const double ya = cy * g.dy, yb = (tiles_y * kTileY - 1 - cy) * g.dy;
@@ -761,11 +808,12 @@ int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_beg
     CUtensorMap tmap;
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r;
-    if (NV == 2) {
-        // x (elements), view half (view s -> s + P), row, view
-        const cuuint64_t dims[4] = {(cuuint64_t)p->pk_nu * 4, 2, (cuuint64_t)p->pk_rows, (cuuint64_t)q_views};
+    if (NV >= 2) {
+        // x (elements), slot (view s -> s + np/NV -> ...), row, view
+        const cuuint64_t dims[4] = {(cuuint64_t)p->pk_nu * 4, (cuuint64_t)NV, (cuuint64_t)p->pk_rows,
+                                    (cuuint64_t)q_views};
         const cuuint64_t strides[3] = {(cuuint64_t)q_pair_off * view_bytes, row_bytes, view_bytes};
-        const cuuint32_t box[4] = {(cuuint32_t)(4 * BW), 2, (cuuint32_t)b.box_h, 1};
+        const cuuint32_t box[4] = {(cuuint32_t)(4 * BW), (cuuint32_t)NV, (cuuint32_t)b.box_h, 1};
         r = enc(&tmap, PkT<T>::TMA, 4, const_cast<void *>(Qp), dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -786,14 +834,15 @@ int launch_packed_t(ifdk_plan_s *p, const PkLaunch &b, const void *Qp, int s_beg
     a.abort_group = p->test_abort_group;
     a.resident = p->n_sm * pk_blocks(NV);
     a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
-    a.ny_cols = NV == 2 ? g.ny / 2 : g.ny;
-    a.tiles_x = (g.nx + kTileX - 1) / kTileX;
+    a.ny_cols = NV >= 2 ? g.ny / 2 : g.ny;
+    a.nx_cols = NV == 4 ? g.nx / 2 : g.nx;
+    a.tiles_x = (a.nx_cols + kTileX - 1) / kTileX;
     a.tiles_y = (a.ny_cols + kTileY - 1) / kTileY;
     a.view_begin = s_begin;
     a.view_count = s_count;
     a.q_view0 = q_view0;
     a.q_pair_off = q_pair_off;
-    a.pair_view_off = g.np / 2;
+    a.pair_view_off = g.np / NV;
     a.box_h = b.box_h;
     a.stages = b.stages;
     a.row0 = p->pk_row0;
@@ -846,16 +895,23 @@ int launch_packed(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin, int 
                   int q_views, float *vol, cudaStream_t stream, const PkZRange &zr)
 {
     if (s_count <= 0) return IFDK_OK;
-    const PkLaunch &b = NV == 2 ? p->pk2[q_dtype] : p->pk[q_dtype];
+    const PkLaunch &b = NV == 4 ? p->pk4[q_dtype] : (NV == 2 ? p->pk2[q_dtype] : p->pk[q_dtype]);
     if (!b.path) return IFDK_ERR_UNSUPPORTED;
-    switch (q_dtype) {
-    case IFDK_F32:
-        return launch_packed_bw<float, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream, zr);
-    case IFDK_F16:
+    if constexpr (NV == 4) {   // quads: FP16 storage only (size_packed)
+        if (q_dtype != IFDK_F16) return IFDK_ERR_UNSUPPORTED;
         return launch_packed_bw<__half, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream, zr);
-    default:
-        return launch_packed_bw<__nv_bfloat16, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol,
-                                                   stream, zr);
+    } else {
+        switch (q_dtype) {
+        case IFDK_F32:
+            return launch_packed_bw<float, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream,
+                                               zr);
+        case IFDK_F16:
+            return launch_packed_bw<__half, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream,
+                                                zr);
+        default:
+            return launch_packed_bw<__nv_bfloat16, NV>(p, b, Qp, s_begin, s_count, q_view0, q_pair_off, q_views, vol,
+                                                       stream, zr);
+        }
     }
 }
 
@@ -870,7 +926,7 @@ int plan_view_split(ifdk_plan_s *p)
     p->split_stride = (nvox + 3) / 4 * 4;   // keeps every partial volume 16-byte aligned
     bool small = false;
     for (int d = 0; d < 3; ++d)
-        for (const PkLaunch *b : {&p->pk[d], &p->pk2[d]})
+        for (const PkLaunch *b : {&p->pk[d], &p->pk2[d], &p->pk4[d]})
             if (b->path && (long long)b->grid_x * b->grid_y * 2 <= (long long)p->n_sm * pk_blocks(b->nv)) small = true;
     if (!small) return IFDK_OK;
     const size_t cap = std::min<size_t>(kPkMaxSplits, kPkSplitBytes / (p->split_stride * sizeof(float)));
@@ -883,9 +939,9 @@ int plan_view_split(ifdk_plan_s *p)
     return IFDK_OK;
 }
 
-int packed_view_split(const ifdk_plan_s *p, int q_dtype, int units, bool pairs)
+int packed_view_split(const ifdk_plan_s *p, int q_dtype, int units, int nv)
 {
-    const PkLaunch &b = pairs ? p->pk2[q_dtype] : p->pk[q_dtype];
+    const PkLaunch &b = nv == 4 ? p->pk4[q_dtype] : (nv == 2 ? p->pk2[q_dtype] : p->pk[q_dtype]);
     return b.path ? pk_splits(p, b, units, b.grid_y) : 1;
 }
 
@@ -920,6 +976,7 @@ void plan_packed(ifdk_plan_s *p)
     for (int t = 0; t < 3; ++t) {
         p->pk[t] = size_packed(p, t, 1);
         p->pk2[t] = p->pk[t].path ? size_packed(p, t, 2) : PkLaunch{};
+        p->pk4[t] = p->pk2[t].path ? size_packed(p, t, 4) : PkLaunch{};
     }
 }
 
@@ -956,12 +1013,22 @@ int launch_packed_pairs(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin
     return launch_packed<2>(p, Qp, q_dtype, s_begin, s_count, q_view0, q_pair_off, q_views, vol, stream, PkZRange{});
 }
 
+int launch_packed_quads(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin, int s_count, int q_view0,
+                        int q_slot_off, int q_views, float *vol, cudaStream_t stream)
+{
+    return launch_packed<4>(p, Qp, q_dtype, s_begin, s_count, q_view0, q_slot_off, q_views, vol, stream, PkZRange{});
+}
+
 int launch_backproject_packed(ifdk_plan_s *p, const void *Qp, int q_dtype, int view_begin, int view_count,
                               int q_view0, int q_views, float *vol, cudaStream_t stream, const PkZRange &zr)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return IFDK_ERR_CUDA;
     const int b = view_begin, e = view_begin + view_count, h = p->g.np / 2;
+    // the whole scan in quarter-turn quads (s, s + np/4, s + np/2, s + 3np/4), s < np/4
+    if (p->use_quarter_turn && p->pk4[q_dtype].path && b == 0 && e == p->g.np && q_view0 == 0 &&
+        q_views == p->g.np)
+        return launch_packed<4>(p, Qp, q_dtype, 0, p->g.np / 4, 0, p->g.np / 4, p->g.np, vol, stream, zr);
     int m = b;
     if (p->use_half_turn && p->pk2[q_dtype].path) split_half_turn(p->g.np, b, e, &m);
     if (m == b) return launch_packed<1>(p, Qp, q_dtype, b, view_count, q_view0, 0, q_views, vol, stream, zr);

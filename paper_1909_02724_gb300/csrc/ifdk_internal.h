@@ -50,10 +50,11 @@ constexpr int kPkMaxStages = 8;
 constexpr int kPkBoxS = 32, kPkBoxL = 48;   // box widths (elements) the kernel is built for
 // z pairs per thread: 16 for single views; with half-turn view pairs (two
 // columns' runs in registers) 16 for FP16 storage and 12 for FP32 / BF16,
-// whose wider taps need the registers.  A multiple of 4 (vector writes).
-constexpr int pk_pairs(int nv, int q_dtype) { return nv == 2 && q_dtype != IFDK_F16 ? 12 : 16; }
+// whose wider taps need the registers; with quarter-turn view quads (four
+// columns' runs) 8.  A multiple of 4 (vector writes).
+constexpr int pk_pairs(int nv, int q_dtype) { return nv == 4 ? 8 : (nv == 2 && q_dtype != IFDK_F16 ? 12 : 16); }
 // resident blocks per SM the packed kernel is built for (registers) and sized for (shared memory)
-constexpr int pk_blocks(int nv) { return nv == 2 ? 2 : 3; }
+constexpr int pk_blocks(int nv) { return nv >= 2 ? 2 : 3; }
 // z pairs of the blocks after the full L-pair z-blocks (the volume's remainder)
 constexpr int kPkTailL = 4;
 // z-blocks of a packed launch: npairs / L full blocks, then tail blocks of kPkTailL pairs
@@ -105,9 +106,11 @@ struct ifdk_plan_s {
     // holds pk_nu elements (columns -1 .. nu - 1, rounded up to even) of 4 values each
     int pk_rows = 0, pk_nu = 0, pk_row0 = 0;   // pk_row0: detector row of packed row 0 (<= 0)
     float pk_wscale = 1.0f;              // power of two putting the largest FP16 weight in [1, 2)
-    ifdk::PkLaunch pk[3], pk2[3];        // per storage type: single views / half-turn view pairs
+    ifdk::PkLaunch pk[3], pk2[3], pk4[3];   // per storage type: single views / half-turn pairs / quarter-turn quads
     bool half_turn = false;              // view s + np/2 is view s turned by pi (exactly)
+    bool quarter_turn = false;           // also view s + np/4 is view s turned by pi/2 (exactly)
     bool use_half_turn = true;           // caller switch (ifdk_set_view_pairing)
+    bool use_quarter_turn = false;       // caller switch (ifdk_set_view_pairing mode 2)
     // short scan: 2 w(beta_s, gamma_u) per (view, column), [np][nu] (nullptr: full scan)
     float *d_sweight = nullptr;
     // view split: partial volumes [split_cap][split_stride] (allocated only for
@@ -166,6 +169,10 @@ int launch_backproject_packed(ifdk_plan_s *p, const void *Qp, int q_dtype, int v
 // is packed view s - q_view0 and its partner packed view s - q_view0 + q_pair_off.
 int launch_packed_pairs(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin, int s_count, int q_view0,
                         int q_pair_off, int q_views, float *vol, cudaStream_t stream);
+// Quarter-turn quads (s, s + np/4, s + np/2, s + 3np/4) for s in [s_begin, s_begin + s_count);
+// view s + k np/4 is packed view s - q_view0 + k q_slot_off.
+int launch_packed_quads(ifdk_plan_s *p, const void *Qp, int q_dtype, int s_begin, int s_count, int q_view0,
+                        int q_slot_off, int q_views, float *vol, cudaStream_t stream);
 // The views of [b, e) that pair up: s in [b, *m) with partners in [b + np/2, *m + np/2);
 // the rest are [*m, b + np/2) and [*m + np/2, e).  *m = b when nothing pairs.
 void split_half_turn(int np, int b, int e, int *m);
@@ -173,7 +180,7 @@ void split_half_turn(int np, int b, int e, int *m);
 // plan creation (small volumes only); the parts a launch over `units` pairs
 // (pairs) or views uses.
 int plan_view_split(ifdk_plan_s *p);
-int packed_view_split(const ifdk_plan_s *p, int q_dtype, int units, bool pairs);
+int packed_view_split(const ifdk_plan_s *p, int q_dtype, int units, int nv);
 int check_backproject_args(const ifdk_plan_s *p, const void *Q, int q_dtype, int view_begin, int view_count,
                            const float *vol);
 }  // namespace ifdk

@@ -90,6 +90,12 @@ int init_host_plan(ifdk_plan_s *p, const ifdk_geometry *gin)
     p->half_turn = g.np >= 2 && g.np % 2 == 0;
     for (int s = 0; p->half_turn && s < g.np / 2; ++s)
         p->half_turn = std::fabs(std::remainder(g.angles[s + g.np / 2] - g.angles[s] - M_PI, 2.0 * M_PI)) < 1e-9;
+    // quarter turn: view s + np/4 is view s turned by pi/2 (with the half turn, so are
+    // s + np/2 and s + 3np/4)
+    p->quarter_turn = p->half_turn && g.np % 4 == 0;
+    for (int s = 0; p->quarter_turn && s < g.np / 4; ++s)
+        p->quarter_turn =
+            std::fabs(std::remainder(g.angles[s + g.np / 4] - g.angles[s] - 0.5 * M_PI, 2.0 * M_PI)) < 1e-9;
 
     // Per-view projection terms, FP64 (Eq. 2: M1 . Mrot(b) . M0, multiplied out
     // in closed form and re-centred on the volume centre and principal point).
@@ -397,10 +403,37 @@ int ifdk_backproject_packed_batch(ifdk_plan p, const void *Qpb, int q_dtype, int
     return rc;
 }
 
+int ifdk_backproject_packed_quads(ifdk_plan p, const void *Qpq, int q_dtype, int view_begin, int view_count,
+                                  float *vol, void *stream)
+{
+    int rc = check_backproject_args(p, Qpq, q_dtype, view_begin, view_count, vol);
+    if (rc != IFDK_OK) return rc;
+    if (!p->pk[q_dtype].path) return IFDK_ERR_UNSUPPORTED;
+    const int q4 = p->g.np / 4;
+    if (p->g.np % 4 != 0 || view_begin + view_count > q4) return IFDK_ERR_INVALID;
+    if (view_count == 0) return IFDK_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return IFDK_ERR_CUDA;
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int n = view_count, b = view_begin;
+    // packed view k n + q of the batch is view b + q + k np/4, k = 0..3
+    if (p->use_quarter_turn && p->pk4[q_dtype].path) return launch_packed_quads(p, Qpq, q_dtype, b, n, b, n, 4 * n, vol, s);
+    if (p->use_half_turn && p->pk2[q_dtype].path) {
+        // slots 0 and 2, then slots 1 and 3, as half-turn pairs
+        rc = launch_packed_pairs(p, Qpq, q_dtype, b, n, b, 2 * n, 4 * n, vol, s);
+        if (rc == IFDK_OK) rc = launch_packed_pairs(p, Qpq, q_dtype, b + q4, n, b + q4 - n, 2 * n, 4 * n, vol, s);
+        return rc;
+    }
+    for (int k = 0; k < 4 && rc == IFDK_OK; ++k)
+        rc = launch_backproject_packed(p, Qpq, q_dtype, b + k * q4, n, b + k * q4 - k * n, 4 * n, vol, s);
+    return rc;
+}
+
 int ifdk_set_view_pairing(ifdk_plan p, int enable)
 {
-    if (!p || (enable != 0 && enable != 1)) return IFDK_ERR_INVALID;
+    if (!p || enable < 0 || enable > 2) return IFDK_ERR_INVALID;
     p->use_half_turn = enable != 0;
+    p->use_quarter_turn = enable == 2;
     return IFDK_OK;
 }
 
@@ -465,8 +498,10 @@ int ifdk_view_split(ifdk_plan p, int q_dtype, int *splits)
 {
     if (!p || !splits) return IFDK_ERR_INVALID;
     if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
-    const bool pairs = p->use_half_turn && p->pk2[q_dtype].path;
-    *splits = packed_view_split(p, q_dtype, pairs ? p->g.np / 2 : p->g.np, pairs);
+    const bool quads = p->use_quarter_turn && p->pk4[q_dtype].path;
+    const bool pairs = !quads && p->use_half_turn && p->pk2[q_dtype].path;
+    const int nv = quads ? 4 : (pairs ? 2 : 1);
+    *splits = packed_view_split(p, q_dtype, p->g.np / nv, nv);
     return IFDK_OK;
 }
 
@@ -546,12 +581,14 @@ int ifdk_backproject_info(ifdk_plan p, int q_dtype, int64_t info[8])
     return IFDK_OK;
 }
 
-// Launch of a full-range packed back-projection: half-turn pairs when they apply.
+// Launch of a full-range packed back-projection: quarter-turn quads or
+// half-turn pairs when they apply (and are switched on).
 static void fill_packed_info(const ifdk_plan_s *p, int q_dtype, int64_t *info)
 {
-    const bool pairs = p->use_half_turn && p->pk2[q_dtype].path;
-    const PkLaunch &b = pairs ? p->pk2[q_dtype] : p->pk[q_dtype];
-    info[0] = b.path ? (pairs ? 2 : 1) : 0;
+    const bool quads = p->use_quarter_turn && p->pk4[q_dtype].path;
+    const bool pairs = !quads && p->use_half_turn && p->pk2[q_dtype].path;
+    const PkLaunch &b = quads ? p->pk4[q_dtype] : (pairs ? p->pk2[q_dtype] : p->pk[q_dtype]);
+    info[0] = b.path ? (quads ? 4 : (pairs ? 2 : 1)) : 0;
     info[1] = b.bw;
     info[2] = b.box_h;
     info[3] = b.pairs;
@@ -575,7 +612,7 @@ int ifdk_backproject_packed_info(ifdk_plan p, int q_dtype, int64_t info[12])
 
 int ifdk_query_packed(const ifdk_geometry *g, int q_dtype, int view_pairing, int64_t info[12])
 {
-    if (!info || (view_pairing != 0 && view_pairing != 1)) return IFDK_ERR_INVALID;
+    if (!info || view_pairing < 0 || view_pairing > 2) return IFDK_ERR_INVALID;
     if (q_dtype != IFDK_F32 && q_dtype != IFDK_F16 && q_dtype != IFDK_BF16) return IFDK_ERR_INVALID;
     int rc = validate(g);
     if (rc != IFDK_OK) return rc;
@@ -584,6 +621,7 @@ int ifdk_query_packed(const ifdk_geometry *g, int q_dtype, int view_pairing, int
     if (rc != IFDK_OK) return rc;
     plan_packed(&tmp);
     tmp.use_half_turn = view_pairing != 0;
+    tmp.use_quarter_turn = view_pairing == 2;
     fill_packed_info(&tmp, q_dtype, info);
     return IFDK_OK;
 }

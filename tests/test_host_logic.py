@@ -186,8 +186,9 @@ def check_packed_windows(g, q_dtype, view_pairing=True, blocks=None, pair0=0, pc
     cx, cy, cz = (g.nx - 1) / 2, (g.ny - 1) / 2, (g.nz - 1) / 2
     uc, vc = (g.nu - 1) / 2 + g.off_u / g.du, (g.nv - 1) / 2 + g.off_v / g.dv
     two_vc = int(round(2 * vc))
-    ny_cols = g.ny // 2 if info["path"] == 2 else g.ny
-    tiles_x, tiles_y = -(-g.nx // TILE), -(-ny_cols // TILE)
+    ny_cols = g.ny // 2 if info["path"] in (2, 4) else g.ny
+    nx_cols = g.nx // 2 if info["path"] == 4 else g.nx
+    tiles_x, tiles_y = -(-nx_cols // TILE), -(-ny_cols // TILE)
     npairs = (g.nz + 1) // 2
     if pcount is None:
         zblocks = packed_zblocks(npairs, L)
@@ -261,6 +262,35 @@ def test_packed_windows_contain_every_tap(geom, dtype):
     for pairing in (True, False):
         info = check_packed_windows(geom, dtype, view_pairing=pairing)
         assert info["path"] == (2 if pairing and geom.ny % 2 == 0 and geom.np % 2 == 0 else 1)
+
+
+@pytest.mark.parametrize("geom", [
+    scaled_geometry(64, 64, 64),
+    scaled_geometry(48, 64, 40, nz=42),
+    scaled_geometry(32, 48, 16, nz=33),
+    circular(12, 64, 48, 1.5, 1.5, 36, 36, 22, 1.0, off_u=-0.4, off_v=-4.5),
+])
+def test_quad_windows_contain_every_tap(geom):
+    """Quarter-turn quads (FP16 storage): the quadrant's tiles and every view."""
+    info = check_packed_windows(geom, B.IFDK_F16, view_pairing=2)
+    assert info["path"] == 4
+    assert B.ifdk_query_packed(geom, B.IFDK_F32, 2)["path"] == 2      # quads are FP16 only
+    assert B.ifdk_query_packed(geom, B.IFDK_F16, 1)["path"] == 2
+
+
+def test_quad_detection():
+    """Path 4 needs np % 4 == 0 with exact quarter turns and a square, even column grid."""
+    g = scaled_geometry(32, 48, 16)
+    assert B.ifdk_query_packed(g, B.IFDK_F16, 2)["path"] == 4
+    assert B.ifdk_query_packed(g.with_(angles=g.angles[:14]), B.IFDK_F16, 2)["path"] in (1, 2)  # np % 4 != 0
+    assert B.ifdk_query_packed(g.with_(ny=30), B.IFDK_F16, 2)["path"] == 2            # not square
+    assert B.ifdk_query_packed(g.with_(dy=g.dx * 1.01), B.IFDK_F16, 2)["path"] == 2   # pitches differ
+    six = circular(18, 48, 48, 96 / 48, 96 / 48, 32, 32, 32, 2.0)                    # 18 views: no quarter turn
+    assert B.ifdk_query_packed(six, B.IFDK_F16, 2)["path"] == 2
+    jitter = g.angles.copy()
+    jitter[g.np // 4 + 1] += 1e-6
+    jitter[3 * g.np // 4 + 1] += 1e-6                                                # half turns still exact
+    assert B.ifdk_query_packed(g.with_(angles=jitter), B.IFDK_F16, 2)["path"] == 2
 
 
 def test_packed_path_declines_wide_footprints():
