@@ -68,13 +68,18 @@ def parse():
     ap.add_argument("--solver", choices=["sart", "mlem"], default=None,
                     help="time iterations of an iterative solver instead of FDK (e.g. --workload grad256)")
     ap.add_argument("--subsets", type=int, default=10, help="ordered view subsets of --solver")
+    ap.add_argument("--unrolled", type=int, default=0,
+                    help="time this many unrolled gradient-descent steps (forward + backward, e.g. grad256)")
+    ap.add_argument("--filter-views", type=int, default=0,
+                    help="time only the filtering stage on this many views of the workload")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-view-pairing", action="store_true",
                     help="back-project every view singly (no half-turn view pairs)")
-    ap.add_argument("--pairing", type=int, default=2, choices=[1, 2],
-                    help="1: half-turn view pairs; 2: quarter-turn quads where they apply (FP16), pairs elsewhere")
+    ap.add_argument("--pairing", type=int, default=1, choices=[1, 2],
+                    help="1: half-turn view pairs (the faster); 2: quarter-turn quads where they apply (FP16), "
+                         "pairs elsewhere")
     ap.add_argument("--view-split", type=int, default=0,
                     help="cap on the view split of small volumes (0 automatic, 1 off)")
     ap.add_argument("--standard", action="store_true",
@@ -329,11 +334,11 @@ class Arm:
         self.bf = BatchFdk(plan, batches, dtype=tdt, device=dev, packed=not standard, group=group)
         self.vol = torch_empty_vol(g, dev)
 
-    def step(self, E, k, ev=None):
+    def step(self, E, k, ev=None, ev_filter=None):
         b = k % self.bf.batches
         if b == 0:
             self.vol.zero_()
-        self.bf.step(E, self.vol, b, ev_bp=ev)
+        self.bf.step(E, self.vol, b, ev_bp=ev, ev_filter=ev_filter)
 
     def updates(self, k) -> int:
         g = self.bf.plan.geom
@@ -399,6 +404,8 @@ def run_ours(args):
     clocks = ClockSampler(local)
     bp_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                  for _ in range(args.steps)]
+    f_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks.start()
     time.sleep(0.3)
@@ -407,7 +414,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0.record(stream)
     for k in range(args.steps):
-        arm.step(E, k, bp_events[k])
+        arm.step(E, k, bp_events[k], f_events[k])
     t1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -418,6 +425,7 @@ def run_ours(args):
     ms = t0.elapsed_time(t1)
     upd_steps = sum(arm.updates(k) for k in range(args.steps))
     bp_ms = [a.elapsed_time(b) for a, b in bp_events]
+    f_ms = float(np.mean([a.elapsed_time(b) for a, b in f_events]))
     bp_gups = float(np.mean([arm.updates(k) / (t * 1e-3) / 2 ** 30 for k, t in enumerate(bp_ms)]))
     ms = max_over_ranks(ms, device=dev)
     ms_per_step = ms / args.steps
@@ -522,6 +530,19 @@ def run_ours(args):
                      "units_per_launch": arm.updates(0)})
 
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    # the filtering stage of a step (split pre-pass + tensor-core Toeplitz GEMM per row chunk):
+    # dense FLOPs 2 rows Nu (Nu + 1) per BF16 term product (6 products for 3 terms, 3 for 2)
+    rows_step = arm.bf.group * arm.bf.n * g.nv
+    products = {3: 6, 2: 3, 1: 1}[terms]
+    f_flops = 2.0 * rows_step * g.nu * (g.nu + 1) * products
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    filter_stage = {"kernels": "filter_split_kernel + filter_tc_kernel per row chunk", "ms_per_step": f_ms,
+                    "split_terms": terms, "term_products": products, "flops_per_step": f_flops,
+                    "achieved": f_flops / (f_ms * 1e-3) / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+                    "bound": "tensor", "frac": f_flops / (f_ms * 1e-3) / 1e12 / bf16_peak,
+                    "frac_split_terms_count": f_flops / products * terms / (f_ms * 1e-3) / 1e12 / bf16_peak,
+                    "peak_basis": "MEASURED_PEAKS bf16_tflops (burst)" if "bf16_tflops" in peaks
+                    else "fallback 1900 TFLOP/s"}
     output_stage = {"kernel": "slices_kernel<float>", "ms_per_launch": sl_ms,
                     "bytes_per_launch": sl_bytes, "achieved": sl_bytes / (sl_ms * 1e-3) / 1e9,
                     "peak": hbm, "unit": "GB/s", "bound": "hbm",
@@ -572,7 +593,8 @@ def run_ours(args):
                        if packed else "filtered views as stored",
                        "bp_launch": info, "view_split": splits},
             "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roofline,
-            "storage_arms": storage_arms, "cpu_baseline": cpu, "output_stage": output_stage,
+            "storage_arms": storage_arms, "cpu_baseline": cpu, "filter_stage": filter_stage,
+            "output_stage": output_stage,
             "arith_rates": {k: (v if k == "n_sm" else {"lane_ops_per_clk_sm": round(v["lane_ops_per_clk_sm"], 2),
                                                         "warp_instr_per_clk_sm": round(v["warp_instr_per_clk_sm"], 3)})
                             for k, v in rates.items()},
@@ -837,10 +859,129 @@ def run_solver(args):
     print(json.dumps(line), flush=True)
 
 
+def run_filter(args):
+    """--filter-views N: the filtering stage alone (ifdk_filter_views, tensor cores) on the
+    first N views of the workload (a small case of the step's filter, for profiling)."""
+    import torch
+    from paper_1909_02724_gb300 import binding as B
+    from paper_1909_02724_gb300.build import build
+    from paper_1909_02724_gb300.phantom import line_integrals_gpu, workload
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    build()
+    w = workload(args.workload)
+    g = w.geom
+    n = min(args.filter_views, g.np)
+    tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.dtype]
+    plan = B.Plan(g)
+    E = line_integrals_gpu(w.phantom(), g, view_count=n)
+    Q = torch.empty(E.shape, dtype=tdt, device="cuda")
+    terms = 3 if tdt == torch.float32 else 2
+    for _ in range(max(3, args.warmup)):
+        plan.filter_views(E, Q, view_begin=0, split_terms=terms)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        a.record(stream)
+        plan.filter_views(E, Q, view_begin=0, split_terms=terms)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    products = {3: 6, 2: 3, 1: 1}[terms]
+    flops = 2.0 * n * g.nv * g.nu * (g.nu + 1) * products
+    peak = float(measured_peaks().get("bf16_tflops", 1900.0))
+    print(json.dumps({"metric": "filtering stage TFLOP/s (dense Toeplitz, BF16 term products)",
+                      "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": args.dtype,
+                      "config": {"workload": workload_desc(w) + f"; first {n} views", "split_terms": terms,
+                                 "term_products": products},
+                      "roofline": {"bound": "tensor", "achieved": flops / (ms * 1e-3) / 1e12, "peak": peak,
+                                   "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / 1e12 / peak}}), flush=True)
+
+
+def run_unrolled(args):
+    """--unrolled T: the differentiation workload (grad256): T unrolled gradient-descent
+    steps on ||A x - y||^2 (A = ifdk_project, A^T the back-projection) with per-step
+    recomputation, forward and backward; a step is one such forward + backward.  Also
+    times one application of each operator on a dense volume."""
+    import torch
+    from paper_1909_02724_gb300 import autograd as A
+    from paper_1909_02724_gb300 import binding as B
+    from paper_1909_02724_gb300.build import build
+    from paper_1909_02724_gb300.phantom import workload, workload_projections_gpu
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    build()
+    w = workload(args.workload)
+    g = w.geom
+    plan = B.Plan(g)
+    y = workload_projections_gpu(w)
+    y = y / y.abs().max()
+    v = torch.randn((g.nx, g.ny, g.nz), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    for _ in range(8):                    # power iteration on A^T A for the step size
+        v = plan.backproject(plan.project(v))
+        lam = float(v.norm())
+        v /= lam
+    T = args.unrolled
+
+    def once():
+        alphas = torch.full((T,), 0.5 / lam, device="cuda", requires_grad=True)
+        x = A.unrolled_gd(plan, y, torch.zeros((g.nx, g.ny, g.nz), device="cuda"), alphas, recompute=True)
+        r = A.project(x, plan) - y
+        (r * r).sum().backward()
+        return alphas.grad
+
+    for _ in range(max(1, args.warmup)):
+        once()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        once()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    ops = T * 6 + 2          # forward, recomputed forward, the two transposes per step; the loss
+    # one application of each operator on a dense volume / dense views
+    xd = plan.backproject(plan.filter(workload_projections_gpu(w)))
+    P = torch.zeros_like(y)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    plan.project(xd, P)
+    P.zero_()
+    ev[0].record(stream)
+    plan.project(xd, P)
+    ev[1].record(stream)
+    A.backproject(P, plan)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    pj, bp = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    print(json.dumps({"metric": "unrolled gradient descent GUPS (operator updates: (6 T + 2) Nx Ny Nz Np per "
+                                "forward + backward / T / 2^30)",
+                      "value": ops * g.updates / (ms * 1e-3) / 2 ** 30, "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": workload_desc(w), "unrolled_steps": T, "recompute": True},
+                      "project_ms_per_application": pj, "backproject_ms_per_application": bp,
+                      "project_gups": g.updates / (pj * 1e-3) / 2 ** 30,
+                      "backproject_gups": g.updates / (bp * 1e-3) / 2 ** 30}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.unrolled:
+        run_unrolled(args)
+    elif args.filter_views:
+        run_filter(args)
     elif args.solver:
         run_solver(args)
     elif args.workload == "slab4096":

@@ -145,21 +145,26 @@ class BatchFdk:
         s0 = b * self.n
         return s0, max(0, min(self.n, self.part - s0))
 
-    def step(self, E: torch.Tensor, vol: torch.Tensor, b: int, stream=None, ev_bp=None) -> None:
+    def step(self, E: torch.Tensor, vol: torch.Tensor, b: int, stream=None, ev_bp=None, ev_filter=None) -> None:
         """Batch b of the scan E (float32 CUDA [np][nv][nu], or a buffer holding just this
-        batch: its n views, then their n partners, n = views(b)[1]) added into vol.  ev_bp: optional
-        (start, end) CUDA events recorded around the back-projection launch."""
+        batch: its group parts of n views each, n = views(b)[1]) added into vol.  ev_bp,
+        ev_filter: optional (start, end) CUDA events recorded around the back-projection
+        launch and around the filter calls."""
         g = self.plan.geom
         s0, n = self.views(b)
         if n == 0:
             return
         K = self.group
+        s = torch.cuda.current_stream() if stream is None else stream
+        if ev_filter is not None:
+            ev_filter[0].record(s)
         for k in range(K):
             v0 = s0 + k * self.part
             Ek = E[v0:v0 + n] if E.shape[0] == g.np else E[k * n:(k + 1) * n]
             self.plan.filter_views(Ek, self.Q[k * n:(k + 1) * n], view_begin=v0, split_terms=self.split_terms,
                                    stream=stream)
-        s = torch.cuda.current_stream() if stream is None else stream
+        if ev_filter is not None:
+            ev_filter[1].record(s)
         if self.packed:
             Qpb = self.Qp[:K * n]
             self.plan.pack(self.Q[:K * n], Qpb, stream=stream)

@@ -103,8 +103,9 @@ def test_pair_range_over_the_whole_scan_takes_quads():
     part = plan.backproject_packed_pairs(Qp, 3, 6)
     torch.cuda.synchronize()
     nz_out = part.shape[2]
-    assert rel(part[:, :, :6], whole[:, :, 3:9]) <= 1e-5
-    assert rel(part[:, :, nz_out - 6:], whole[:, :, g.nz - 9:g.nz - 3]) <= 1e-5
+    # the pair-range launch sums each block's views in another order (FP16 products, FP32 sums)
+    assert rel(part[:, :, :6], whole[:, :, 3:9]) <= 5e-5
+    assert rel(part[:, :, nz_out - 6:], whole[:, :, g.nz - 9:g.nz - 3]) <= 5e-5
 
 
 def test_non_square_grid_falls_back_to_pairs():
