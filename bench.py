@@ -153,6 +153,17 @@ def parse_clock_samples(out: str) -> dict:
             "samples": len(sm)}
 
 
+def host_memory_available() -> int:
+    """MemAvailable of /proc/meminfo in bytes (a large number where it cannot be read)."""
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 1 << 62
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -464,7 +475,15 @@ def run_ours(args):
     # step copies its batch of projections in; every finished reconstruction copies its
     # volume out; the copies overlap the computation of the neighbouring steps
     e2e = None
-    if not args.no_e2e:
+    # the host leg pins the scan and one volume per rank: skip it (and say so) where the
+    # host cannot hold that for every rank of this node
+    pin_bytes = (E.numel() + arm.vol.numel()) * 4
+    local_world = int(os.environ.get("LOCAL_WORLD_SIZE", world))
+    need = pin_bytes * local_world + (8 << 30)
+    host_ok = host_memory_available() > need
+    if not args.no_e2e and not host_ok:
+        e2e = {"skipped": f"host memory below {need / 2**30:.0f} GiB for the pinned buffers of {local_world} ranks"}
+    if not args.no_e2e and host_ok:
         E_host = torch.empty(E.shape, dtype=torch.float32, pin_memory=True)
         E_host.copy_(E)
         vol_host = torch.empty(arm.vol.shape, dtype=torch.float32, pin_memory=True)

@@ -110,6 +110,35 @@ def test_fdk2048_all_storage_types():
     run("fdk2048", ["f32", "f16", "bf16"], vox)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_fdk2048_in_batches_as_the_bench_runs_it(dtype):
+    """The benchmark's launch configuration: fdk2048 in 4 batches of 256 half-turn
+    pairs (ifdk_filter_views, ifdk_pack_views, ifdk_backproject_packed_batch), against
+    the FP64 oracle on sampled voxels of the top, middle and bottom slices."""
+    from paper_1909_02724_gb300.api import BatchFdk
+    from paper_1909_02724_gb300.binding import Plan
+    w = workload("fdk2048")
+    g = w.geom
+    vox = slices(g, [0, 1023, 1024, 2047], 16)
+    E = workload_projections_gpu(w)
+    ref = oracle_on_sample(g, E, vox)
+    plan = Plan(g)
+    bf = BatchFdk(plan, 4, dtype=getattr(torch, DTYPES[dtype]))
+    vol = torch.zeros((g.nx, g.ny, g.nz), device="cuda")
+    bf.reconstruct(E, vol)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    idx = [torch.from_numpy(vox[:, c]).cuda() for c in range(3)]
+    v = vol[idx[0], idx[1], idx[2]].double().cpu().numpy()
+    err = float(np.linalg.norm(v - ref) / np.linalg.norm(ref))
+    mx = float(np.max(np.abs(v - ref))) / float(vol.abs().max())
+    print(f"fdk2048 batches {dtype}: rel-L2 {err:.2e}, max-abs/max {mx:.2e}")
+    if dtype == "f32":
+        assert err <= 1e-5 and mx <= 1e-4, (err, mx)
+    else:
+        assert err <= 2e-3, err
+
+
 def test_view_and_slab_decomposition():
     """The paper's R x C grid on one GPU: a view split (columns) sums to the whole
     back-projection; z-slabs with their own plans (rows; off-centre slabs take
