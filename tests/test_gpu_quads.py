@@ -18,6 +18,7 @@ import pytest
 import oracle
 from paper_1909_02724_gb300 import binding as B
 from paper_1909_02724_gb300.phantom import line_integrals, scaled_geometry, workload
+from tests.random_geometries import random_square_geometries
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -63,6 +64,24 @@ def test_quads_match_the_oracle_and_the_pairs(name):
     torch.cuda.synchronize()
     assert plan.device_status() == B.IFDK_OK
     # the same sum in another order (and the quad's coordinates come from the own view's terms)
+    assert rel(quads, pairs) <= 5e-5
+    ref = oracle.backproject(g, Q.float().double().cpu().numpy())
+    assert rel_np(quads.cpu().numpy(), ref) <= 2e-3
+
+
+@pytest.mark.parametrize("name", [n for n, _ in random_square_geometries()])
+def test_quads_on_random_square_geometries(name):
+    g = dict(random_square_geometries())[name]
+    plan = B.Plan(g)
+    Q = random_views(g, torch.float16, seed=len(name))
+    Qp = plan.pack(Q)
+    plan.set_view_pairing(2)
+    assert plan.packed_info(torch.float16)["path"] == 4
+    quads = plan.backproject_packed(Qp)
+    plan.set_view_pairing(1)
+    pairs = plan.backproject_packed(Qp)
+    torch.cuda.synchronize()
+    assert plan.device_status() == B.IFDK_OK
     assert rel(quads, pairs) <= 5e-5
     ref = oracle.backproject(g, Q.float().double().cpu().numpy())
     assert rel_np(quads.cpu().numpy(), ref) <= 2e-3

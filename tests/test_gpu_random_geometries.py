@@ -3,7 +3,7 @@
 Random detector and volume sizes (odd and even), pitches, source distances,
 offsets, start angles and view counts: the tensor-core filter, both
 back-projectors (packed with and without view pairing where the plan has
-them), FP16 storage and the adjoint, each against the FP64 oracle.  The same
+them), FP16 storage (pairs and, where the scan allows, quads) and the adjoint, each against the FP64 oracle.  The same
 geometries pass the host emulation of the packed windows on the CPU."""
 import numpy as np
 import pytest
@@ -50,8 +50,11 @@ def test_random_geometry_parity(name):
             assert rel_l2(vp, ref) <= 1e-5, pairing
             assert np.abs(vp - ref).max() <= 1e-4 * np.abs(ref).max()
         Q16 = plan.filter(Ed, dtype=torch.float16)
-        v16 = plan.backproject_packed(plan.pack(Q16)).cpu().double().numpy()
-        assert rel_l2(v16, ref) <= 2e-3
+        Qp16 = plan.pack(Q16)
+        for mode in (1, 2):          # half-turn pairs; quarter-turn quads where the geometry has them
+            plan.set_view_pairing(mode)
+            v16 = plan.backproject_packed(Qp16).cpu().double().numpy()
+            assert rel_l2(v16, ref) <= 2e-3, mode
     x = rng.standard_normal((g.nx, g.ny, g.nz)).astype(np.float32)
     P = plan.project(torch.from_numpy(x).cuda()).cpu().double().numpy()
     assert rel_l2(P, oracle.project(g, x.astype(np.float64))) <= 1e-5

@@ -278,6 +278,20 @@ def test_quad_windows_contain_every_tap(geom):
     assert B.ifdk_query_packed(geom, B.IFDK_F16, 1)["path"] == 2
 
 
+def test_quad_windows_random_square_geometries():
+    """Seeded square geometries (quads apply): whole-volume and random pair-range
+    launches keep every tap of every block in its window."""
+    from tests.random_geometries import random_square_geometries
+    rng = np.random.default_rng(9)
+    for _, g in random_square_geometries():
+        info = check_packed_windows(g, B.IFDK_F16, view_pairing=2)
+        assert info["path"] == 4
+        npairs = (g.nz + 1) // 2
+        pb = int(rng.integers(0, npairs))
+        pc = int(rng.integers(1, npairs - pb + 1))
+        check_packed_windows(g, B.IFDK_F16, 2, pair0=pb, pcount=pc)
+
+
 def test_quad_detection():
     """Path 4 needs np % 4 == 0 with exact quarter turns and a square, even column grid."""
     g = scaled_geometry(32, 48, 16)
