@@ -316,16 +316,17 @@ def path_ceilings(rates: dict, n_sm: int, f_hz: float) -> dict:
     instruction mix that storage's path needs per update, at the measured rates
     (times of the different kinds added: they share the FMA issue):
       f32:  the ten FP32 operations;
-      bf16: the ten FP32 operations + 2 integer ops widening the one new packed
-            row word pair per update (lop3 rate);
+      bf16: the ten FP32 operations, the u-lerp's two among them as FP32 FMAs
+            of BF16 inputs (fma.rn.f32.bf16 rate: weights 1 - du and du on the
+            stored taps, which are never widened);
       f16:  v, floor, fraction in FP32 (3), the three lerps in half2 (6 FP16
             lanes) and the accumulate as one FP16-product FP32 FMA."""
     r32 = max(rates["ffma"]["lane_ops_per_clk_sm"], rates["ffma2"]["lane_ops_per_clk_sm"])
     rh = rates["hfma2"]["lane_ops_per_clk_sm"]
     rm = rates["fma_f32_f16"]["lane_ops_per_clk_sm"]
-    ri = rates["lop3"]["lane_ops_per_clk_sm"]
+    rb = rates["fma_f32_bf16"]["lane_ops_per_clk_sm"]
     per_clk = {"f32": 1.0 / (FP32_OPS_PER_UPDATE / r32),
-               "bf16": 1.0 / (FP32_OPS_PER_UPDATE / r32 + 2.0 / ri),
+               "bf16": 1.0 / ((FP32_OPS_PER_UPDATE - 2) / r32 + 2.0 / rb),
                "f16": 1.0 / (3.0 / r32 + 6.0 / rh + 1.0 / rm)}
     scale = n_sm * f_hz / 2 ** 30
     return {"alu10": r32 / FP32_OPS_PER_UPDATE * scale, "fp32_lane_ops_per_clk_sm": r32,

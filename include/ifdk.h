@@ -220,9 +220,14 @@ int ifdk_backproject_views(ifdk_plan p, const void *Qv, int q_dtype, int view_be
    c = e - 1 (row_elems = nu + 1 rounded up to even) and holds
      Q[r][c], Q[2 v_c - r][c], Q[r][c+1] - Q[r][c], Q[2 v_c - r][c+1] - Q[2 v_c - r][c],
    where Q reads 0 outside the detector; the differences are formed in FP32
-   from the stored values and rounded once to q_dtype.  That is about twice
+   from the stored values and rounded once to q_dtype.  For IFDK_BF16 the
+   element holds the right taps instead of the differences:
+     Q[r][c], Q[2 v_c - r][c], Q[r][c+1], Q[2 v_c - r][c+1]
+   (every value a stored value; the kernel interpolates along U with BF16
+   weights 1 - du and du and FP32 sums).  That is about twice
    the bytes of a view of Q; one shared-memory load then gives a voxel pair
-   both taps of a detector row, and interpolating along U is one FMA.
+   both taps of a detector row, and interpolating along U is one FMA (two for
+   BF16).
    ifdk_packed_size reports view_bytes (bytes of one packed view), rows and
    row_elems (any pointer may be NULL). */
 int ifdk_packed_size(ifdk_plan p, int q_dtype, size_t *view_bytes, int *rows, int *row_elems);
@@ -510,6 +515,7 @@ int ifdk_query_rows(const ifdk_geometry *g, int view_begin, int view_count, int 
      IFDK_RATE_HFMA2       fma.rn.f16x2      (2: packed FP16 pair)
      IFDK_RATE_FMA_F32_F16 fma.rn.f32.f16    (1: FP16 product, FP32 sum)
      IFDK_RATE_LOP3        lop3.b32          (1: integer logic)
+     IFDK_RATE_FMA_F32_BF16 fma.rn.f32.bf16  (1: BF16 product, FP32 sum)
    Each block records its SM clock (clock64) before and after its loop and its
    SM id: clocks[3 b + 0..2] = start, end, smid (device int64 [3 * blocks],
    8-byte aligned).  sink: device FP32 [blocks * 1024], overwritten with the
@@ -519,7 +525,7 @@ int ifdk_query_rows(const ifdk_geometry *g, int view_begin, int view_count, int 
    instructions (under 3 %) make it a lower bound.  Asynchronous on `stream`.
    The paper has no counterpart. */
 enum { IFDK_RATE_FFMA = 0, IFDK_RATE_FFMA2 = 1, IFDK_RATE_HFMA2 = 2, IFDK_RATE_FMA_F32_F16 = 3,
-       IFDK_RATE_LOP3 = 4 };
+       IFDK_RATE_LOP3 = 4, IFDK_RATE_FMA_F32_BF16 = 5 };
 int ifdk_arith_rate(int kind, int blocks, long long iters, float *sink, long long *clocks,
                     int64_t out[2], void *stream);
 

@@ -712,8 +712,10 @@ class Plan:
 
 
 IFDK_RATE_FFMA, IFDK_RATE_FFMA2, IFDK_RATE_HFMA2, IFDK_RATE_FMA_F32_F16, IFDK_RATE_LOP3 = 0, 1, 2, 3, 4
+IFDK_RATE_FMA_F32_BF16 = 5
 RATE_KINDS = {"ffma": IFDK_RATE_FFMA, "ffma2": IFDK_RATE_FFMA2, "hfma2": IFDK_RATE_HFMA2,
-              "fma_f32_f16": IFDK_RATE_FMA_F32_F16, "lop3": IFDK_RATE_LOP3}
+              "fma_f32_f16": IFDK_RATE_FMA_F32_F16, "lop3": IFDK_RATE_LOP3,
+              "fma_f32_bf16": IFDK_RATE_FMA_F32_BF16}
 
 
 def arith_rates(device=None, iters: int = 2048, kinds=tuple(RATE_KINDS)) -> dict:

@@ -10,7 +10,10 @@
 // carries the first column as its right tap), so one shared-memory
 // load gives both voxels of a pair the two taps of a detector row, and the
 // interpolation along u is one FMA per pair (the difference is formed in
-// FP32 when packing, then stored in the storage type).  Packing
+// FP32 when packing, then stored in the storage type).  BF16 storage keeps
+// the right taps themselves, (Q[r][c], Q[2vc-r][c], Q[r][c+1], Q[2vc-r][c+1]):
+// every value is a stored value, exact, and the interpolation along u is two
+// FP32 FMAs of BF16 inputs per voxel.  Packing
 // is one pass over Q (ifdk_pack_views); the back-projection then stages
 // windows of packed views with TMA and uses them as they land.
 //
@@ -59,9 +62,12 @@
 //     previous pair (after a step of two rows, it loads both);
 //   * FP32 accumulation in registers over all views, one read-modify-write of
 //     each thread's z-runs at the end (vectorised, 64-bit offsets, k-major).
-//   FP32 / BF16 storage: taps are interpolated in packed f32x2 arithmetic
-//   (BF16 widened by a shift first); FP16 storage: both lerps in packed half2,
-//   widened once before the FP32 accumulate.
+//   FP32 storage: taps are interpolated in packed f32x2 arithmetic; BF16
+//   storage: the u-lerp is (1 - du) Q_c + du Q_{c+1} as two FP32 FMAs of
+//   BF16 inputs (fma.rn.f32.bf16: the weights rounded to BF16, products
+//   exact, FP32 sum), so the taps are never widened, then the v-lerp and
+//   accumulate in f32x2; FP16 storage: both lerps in packed half2, widened
+//   once before the FP32 accumulate.
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -143,11 +149,6 @@ __device__ __forceinline__ void sts_f32x4(uint32_t a, float4 v)
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
                  : "memory");
 }
-__device__ __forceinline__ void sts_i32x4(uint32_t a, int4 v)
-{
-    asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
-                 : "memory");
-}
 __device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v)
 {
     asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
@@ -207,15 +208,18 @@ __device__ __forceinline__ float rcp_nr(float z)
     return r * fmaf(-z, r, 2.0f);
 }
 
-// Storage-type specific parts: element size, the u-interpolated (direct,
-// mirror) row of an element and the v-lerp + weighted accumulate of a pair.
+// Storage-type specific parts: element size, the u fraction as the row
+// interpolation takes it (Du), the u-interpolated (direct, mirror) row of an
+// element and the v-lerp + weighted accumulate of a pair.
 template <typename T> struct Tap;
 template <> struct Tap<float> {
     static constexpr uint32_t ES = 16;
     using R = float2;
     using Wt = float2;   // the weight of a pair, as the accumulate takes it
+    using Du = float2;
     __device__ __forceinline__ static Wt weight(float w) { return make_float2(w, w); }
-    __device__ __forceinline__ static R row(const unsigned char *e, float2 du2, __half2)
+    __device__ __forceinline__ static Du frac_u(float du) { return make_float2(du, du); }
+    __device__ __forceinline__ static R row(const unsigned char *e, Du du2)
     {
         const float4 q = *reinterpret_cast<const float4 *>(e);   // (taps at c, differences to c + 1)
         return __ffma2_rn(du2, make_float2(q.z, q.w), make_float2(q.x, q.y));
@@ -231,8 +235,10 @@ template <> struct Tap<__half> {
     // FP16 weight (the plan scales w by a power of two that keeps W in range)
     // for the mixed-precision accumulate below
     using Wt = unsigned short;
+    using Du = __half2;
     __device__ __forceinline__ static Wt weight(float w) { return __half_as_ushort(__float2half_rn(w)); }
-    __device__ __forceinline__ static R row(const unsigned char *e, float2, __half2 duh)
+    __device__ __forceinline__ static Du frac_u(float du) { return __float2half2_rn(du); }
+    __device__ __forceinline__ static R row(const unsigned char *e, Du duh)
     {
         const uint2 q = *reinterpret_cast<const uint2 *>(e);
         const __half2 hx = *reinterpret_cast<const __half2 *>(&q.x), hd = *reinterpret_cast<const __half2 *>(&q.y);
@@ -257,12 +263,32 @@ template <> struct Tap<__nv_bfloat16> {
     static constexpr uint32_t ES = 8;
     using R = float2;
     using Wt = float2;
+    using Du = uint32_t;   // the u weights (1 - du, du), each rounded to BF16 (low, high half)
     __device__ __forceinline__ static Wt weight(float w) { return make_float2(w, w); }
-    __device__ __forceinline__ static R row(const unsigned char *e, float2 du2, __half2)
+    __device__ __forceinline__ static Du frac_u(float du)
+    {
+        return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(1.0f - du)) |
+               ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(du)) << 16);
+    }
+    // element (Q_c direct, Q_c mirror | Q_{c+1} direct, Q_{c+1} mirror): per voxel
+    // du Q_{c+1} (exact: a product of two BF16 values fits FP32), then
+    // + (1 - du) Q_c with one rounding
+    __device__ __forceinline__ static R row(const unsigned char *e, Du wu)
     {
         const uint2 q = *reinterpret_cast<const uint2 *>(e);
-        return __ffma2_rn(du2, make_float2(__uint_as_float(q.y << 16), __uint_as_float(q.y & 0xffff0000u)),
-                          make_float2(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xffff0000u)));
+        float2 r;
+        asm("{\n\t.reg .b16 a0, a1, b0, b1, w0, w1;\n\t.reg .f32 z;\n\t"
+            "mov.b32 {a0, a1}, %2;\n\t"
+            "mov.b32 {b0, b1}, %3;\n\t"
+            "mov.b32 {w0, w1}, %4;\n\t"
+            "mov.f32 z, 0f00000000;\n\t"
+            "fma.rn.f32.bf16 %0, w1, b0, z;\n\t"
+            "fma.rn.f32.bf16 %1, w1, b1, z;\n\t"
+            "fma.rn.f32.bf16 %0, w0, a0, %0;\n\t"
+            "fma.rn.f32.bf16 %1, w0, a1, %1;\n\t}"
+            : "=f"(r.x), "=f"(r.y)
+            : "r"(q.x), "r"(q.y), "r"(wu));
+        return r;
     }
     __device__ __forceinline__ static float2 accum(float2 acc, R lo, R hi, float2 dv2, __half2, Wt W2)
     {
@@ -272,8 +298,10 @@ template <> struct Tap<__nv_bfloat16> {
 
 // The z-run of one (column, view group): pair p samples box rows n_p, n_p + 1
 // at v_p = vb + p sig (window coordinates).  The box holds NV views side by
-// side in each row (HB bytes apart, rows ROWB bytes apart); view 0's taps go
-// to a0 with weight W0, view 1's to a1 with weight W1.  Row reuse by the
+// side in each row (rows ROWB bytes apart); the thread's column n reads the
+// view that feeds it at shared offset cb[n] + row * ROWB (cb[n] = the element's
+// offset in that view's slot) and accumulates it with weight W[n] into
+// acc[n].  Row reuse by the
 // warp's largest step (every lane votes): STEP1 (all sig < 1: n_{p+1} - n_p
 // is 0 or 1) loads only row n_p + 1 and takes row n_p from the previous
 // pair; STEP2 (sig < 2, which the plan guarantees: steps 0, 1 or 2) does the
@@ -300,52 +328,51 @@ __device__ __forceinline__ const unsigned char *chk_row(const unsigned char *e, 
 }
 #define PK_CHK_PARAM , const ChkBox &chk
 #define PK_CHK_ARG , chk
-#define PK_ROW(ptr) Tap<T>::row(chk_row<T>((ptr), chk), du2, duh)
+#define PK_ROW(ptr) Tap<T>::row(chk_row<T>((ptr), chk), dut)
 #else
 #define PK_CHK_PARAM
 #define PK_CHK_ARG
-#define PK_ROW(ptr) Tap<T>::row((ptr), du2, duh)
+#define PK_ROW(ptr) Tap<T>::row((ptr), dut)
 #endif
 
-template <typename T, int NV, int L, uint32_t ROWB, uint32_t HB, Reuse MODE, int G>
-__device__ __forceinline__ void pair_loop(float2 (&acc)[NV][L], const unsigned char *sm, uint32_t base, float sig,
-                                          float vb, float2 du2, __half2 duh,
+template <typename T, int NV, int L, uint32_t ROWB, Reuse MODE>
+__device__ __forceinline__ void pair_loop(float2 (&acc)[NV][L], const unsigned char *sm, const uint32_t (&cb)[NV],
+                                          float sig, float vb, typename Tap<T>::Du dut,
                                           const typename Tap<T>::Wt (&W)[NV] PK_CHK_PARAM)
 {
     using R = typename Tap<T>::R;
-    // box slot n (view s + n np/NV) feeds column (n - G) mod NV of the thread (the
-    // loops over n are unrolled: every index below is a constant)
     R lo[NV], hi[NV];
     float dv;
     uint32_t tv = floor_frac(vb, dv);
-    const unsigned char *e = sm + (base + tv * ROWB);   // 32-bit offset arithmetic wraps the biases away
 #pragma unroll
     for (int n = 0; n < NV; ++n) {
-        lo[n] = PK_ROW(e + n * HB);
-        hi[n] = PK_ROW(e + ROWB + n * HB);
+        const unsigned char *e = sm + (cb[n] + tv * ROWB);
+        lo[n] = PK_ROW(e);
+        hi[n] = PK_ROW(e + ROWB);
     }
 #pragma unroll
     for (int n = 0; n < NV; ++n)
-        acc[(n + NV - G) % NV][0] =
-            Tap<T>::accum(acc[(n + NV - G) % NV][0], lo[n], hi[n], make_float2(dv, dv), __float2half2_rn(dv), W[n]);
+        acc[n][0] = Tap<T>::accum(acc[n][0], lo[n], hi[n], make_float2(dv, dv), __float2half2_rn(dv), W[n]);
 #pragma unroll
     for (int p = 1; p < L; ++p) {
         const uint32_t tn = floor_frac(fmaf((float)p, sig, vb), dv);
-        e = sm + (base + tn * ROWB);
+        const uint32_t to = tn * ROWB;
         const float2 dv2 = make_float2(dv, dv);
         const __half2 dvh = __float2half2_rn(dv);
         if constexpr (MODE == Reuse::ANY) {
 #pragma unroll
             for (int n = 0; n < NV; ++n) {
-                lo[n] = PK_ROW(e + n * HB);
-                hi[n] = PK_ROW(e + ROWB + n * HB);
+                const unsigned char *e = sm + (cb[n] + to);
+                lo[n] = PK_ROW(e);
+                hi[n] = PK_ROW(e + ROWB);
             }
         } else if constexpr (MODE == Reuse::STEP1) {
             const bool moved = tn != tv;
             tv = tn;
 #pragma unroll
             for (int n = 0; n < NV; ++n) {
-                const R hn = PK_ROW(e + ROWB + n * HB);
+                const unsigned char *e = sm + (cb[n] + to);
+                const R hn = PK_ROW(e + ROWB);
                 lo[n] = moved ? hi[n] : lo[n];
                 hi[n] = hn;
             }
@@ -354,16 +381,16 @@ __device__ __forceinline__ void pair_loop(float2 (&acc)[NV][L], const unsigned c
             tv = tn;
 #pragma unroll
             for (int n = 0; n < NV; ++n) {
-                const R hn = PK_ROW(e + ROWB + n * HB);
+                const unsigned char *e = sm + (cb[n] + to);
+                const R hn = PK_ROW(e + ROWB);
                 R ln = step != 0 ? hi[n] : lo[n];
-                if (step == 2) ln = PK_ROW(e + n * HB);
+                if (step == 2) ln = PK_ROW(e);
                 lo[n] = ln;
                 hi[n] = hn;
             }
         }
 #pragma unroll
-        for (int n = 0; n < NV; ++n)
-            acc[(n + NV - G) % NV][p] = Tap<T>::accum(acc[(n + NV - G) % NV][p], lo[n], hi[n], dv2, dvh, W[n]);
+        for (int n = 0; n < NV; ++n) acc[n][p] = Tap<T>::accum(acc[n][p], lo[n], hi[n], dv2, dvh, W[n]);
     }
 }
 
@@ -539,8 +566,8 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
     // column m in the view of slot (G + m) mod NV, so slot n feeds column
     // (n - G) mod NV.
     bool ok = true;
-    auto group = [&](int t, auto g_tag) {
-        constexpr int G = decltype(g_tag)::value;
+    auto group = [&](int t, auto g_slot) {
+        const int G = g_slot;   // a compile-time constant, or t mod NV
         const int st = t % S;
         const uint32_t parity = (uint32_t)(t / S) & 1u;
         // refill the stage group t - 2 used (every warp finished it by now, or soon)
@@ -568,16 +595,27 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
         const uint32_t tu = floor_frac(fmaf(x, f, t2.y), du);
         const float ff = f * f;
         const float wsl[4] = {t2.x, t2.w, t3.x, t3.y};
-        typename Tap<T>::Wt W[NV];
+        typename Tap<T>::Wt Ws[NV];
 #pragma unroll
-        for (int n = 0; n < NV; ++n) W[n] = Tap<T>::weight(wsl[n] * ff);
+        for (int n = 0; n < NV; ++n) Ws[n] = Tap<T>::weight(wsl[n] * ff);
         const float sig = t0.w * f;
         const float vb = fmaf(sig, kp0, fmaf(t1.x, f, t2.z));
         // element (n, cu) at offset base + bits(t_v) * ROWB (mod 2^32): n = bits(t_v) - bias,
         // cu = bits(t_u) - bias
         const uint32_t base = sg + kPkBox + (tu - kFloorBias) * ES - kFloorBias * ROWB;
-        const float2 du2 = make_float2(du, du);
-        const __half2 duh = __float2half2_rn(du);
+        // column m takes box slot (m + G) mod NV
+        typename Tap<T>::Wt W[NV];
+        uint32_t cb[NV];
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            const int n = (m + G) & (NV - 1);
+            W[m] = Ws[0];
+#pragma unroll
+            for (int q = 1; q < NV; ++q)
+                if (n == q) W[m] = Ws[q];
+            cb[m] = base + (uint32_t)n * HB;
+        }
+        const typename Tap<T>::Du dut = Tap<T>::frac_u(du);
         // sig < 1 - 2^-10 keeps fp32 rounding of v_{p+1} - v_p below one row; the
         // plan keeps every sig below 1.9 (two rows at most)
         // (FP32 taps keep the reuse across two-row steps; 16-bit taps load both rows,
@@ -587,20 +625,28 @@ __device__ __forceinline__ void pk_block(const PkArgs &a, const CUtensorMap &tma
         const ChkBox chk{sm + sg + kPkBox, sm + sg + kPkBox + a.box_tx_bytes, a.status};
 #endif
         if (__all_sync(0xffffffffu, sig < 0.9990234375f))
-            pair_loop<T, NV, L, ROWB, HB, Reuse::STEP1, G>(acc, sm, base, sig, vb, du2, duh, W PK_CHK_ARG);
+            pair_loop<T, NV, L, ROWB, Reuse::STEP1>(acc, sm, cb, sig, vb, dut, W PK_CHK_ARG);
         else
-            pair_loop<T, NV, L, ROWB, HB, WIDE, G>(acc, sm, base, sig, vb, du2, duh, W PK_CHK_ARG);
+            pair_loop<T, NV, L, ROWB, WIDE>(acc, sm, cb, sig, vb, dut, W PK_CHK_ARG);
         __syncwarp();
         if (lane == 0) mbar_arrive(s0 + kPkEmpty + 8u * st);
     };
-    for (int t = 0; ok && t < ngroups; t += NV) {
-        group(t, std::integral_constant<int, 0>{});
-        if constexpr (NV >= 2)
-            if (ok) group(t + 1, std::integral_constant<int, 1>{});
-        if constexpr (NV == 4) {
-            if (ok) group(t + 2, std::integral_constant<int, 2>{});
-            if (ok) group(t + 3, std::integral_constant<int, 3>{});
+    if constexpr (sizeof(T) == 4) {
+        // FP32 taps: one copy of the group body per slot rotation G (constant
+        // slot offsets; measured faster for them)
+        for (int t = 0; ok && t < ngroups; t += NV) {
+            group(t, std::integral_constant<int, 0>{});
+            if constexpr (NV >= 2)
+                if (ok) group(t + 1, std::integral_constant<int, 1>{});
+            if constexpr (NV == 4) {
+                if (ok) group(t + 2, std::integral_constant<int, 2>{});
+                if (ok) group(t + 3, std::integral_constant<int, 3>{});
+            }
         }
+    } else {
+        // 16-bit taps: one copy for every rotation (the longer z-runs' unrolled
+        // body NV times over measured slower: instruction fetch)
+        for (int t = 0; ok && t < ngroups; ++t) group(t, t & (NV - 1));
     }
     if (!ok) {
         // record the timeout; every exiting warp waits (bounded) for the last box
@@ -669,10 +715,10 @@ __global__ void __launch_bounds__(kThreads, pk_blocks(NV))
 
 // Packing: element e of row r of view s, column c = e - 1:
 // (Q[r][c], Q[2vc-r][c], Q[r][c+1] - Q[r][c], Q[2vc-r][c+1] - Q[2vc-r][c]),
-// the differences formed in FP32 and rounded once to T.
+// the differences formed in FP32 and rounded once to T; for BF16
+// (Q[r][c], Q[2vc-r][c], Q[r][c+1], Q[2vc-r][c+1]), the stored values.
 __device__ __forceinline__ uint32_t bits16(__half x) { return __half_as_ushort(x); }
 __device__ __forceinline__ uint32_t bits16(__nv_bfloat16 x) { return __bfloat16_as_ushort(x); }
-__device__ __forceinline__ uint32_t bits16(float) { return 0u; }
 struct PackArgs {
     long long n_elems;   // n_views * rows * nu_p
     int nv, nu, nu_p, rows, row0, two_vc;
@@ -695,7 +741,9 @@ __global__ void __launch_bounds__(256) pack_kernel(const T *__restrict__ Q, T *_
         const float q2 = dr && c1 ? Storage<T>::to_float(qv[(long long)r * a.nu + c + 1]) : 0.0f;
         const float q3 = mr && c1 ? Storage<T>::to_float(qv[(long long)rm * a.nu + c + 1]) : 0.0f;
         const T v0 = Storage<T>::from_float(q0), v1 = Storage<T>::from_float(q1);
-        const T v2 = Storage<T>::from_float(q2 - q0), v3 = Storage<T>::from_float(q3 - q1);
+        constexpr bool kRawTaps = std::is_same<T, __nv_bfloat16>::value;
+        const T v2 = Storage<T>::from_float(kRawTaps ? q2 : q2 - q0);
+        const T v3 = Storage<T>::from_float(kRawTaps ? q3 : q3 - q1);
         T *d = P + e * 4;
         if constexpr (sizeof(T) == 4) {
             *reinterpret_cast<float4 *>(d) = make_float4(v0, v1, v2, v3);

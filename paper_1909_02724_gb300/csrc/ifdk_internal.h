@@ -49,10 +49,10 @@ struct BpLaunch {
 constexpr int kPkMaxStages = 8;
 constexpr int kPkBoxS = 32, kPkBoxL = 48;   // box widths (elements) the kernel is built for
 // z pairs per thread: 16 for single views; with half-turn view pairs (two
-// columns' runs in registers) 16 for FP16 storage and 12 for FP32 / BF16,
+// columns' runs in registers) 16 for FP16 / BF16 storage and 12 for FP32,
 // whose wider taps need the registers; with quarter-turn view quads (four
 // columns' runs) 8.  A multiple of 4 (vector writes).
-constexpr int pk_pairs(int nv, int q_dtype) { return nv == 4 ? 8 : (nv == 2 && q_dtype != IFDK_F16 ? 12 : 16); }
+constexpr int pk_pairs(int nv, int q_dtype) { return nv == 4 ? 8 : (nv == 2 && q_dtype == IFDK_F32 ? 12 : 16); }
 // resident blocks per SM the packed kernel is built for (registers) and sized for (shared memory)
 constexpr int pk_blocks(int nv) { return nv >= 2 ? 2 : 3; }
 // z pairs of the blocks after the full L-pair z-blocks (the volume's remainder)

@@ -72,7 +72,8 @@ template <> struct Step<IFDK_RATE_HFMA2> {
     }
 };
 // FP32 accumulate of an FP16 product, d = a * b + d with a, b FP16 (the
-// accumulate of the FP16-storage back-projection)
+// accumulate of the FP16-storage back-projection); the same with BF16 inputs
+// (the u-lerp of the BF16-storage back-projection)
 template <> struct Step<IFDK_RATE_FMA_F32_F16> {
     using V = float;
     static constexpr int LANES = 1;
@@ -84,7 +85,20 @@ template <> struct Step<IFDK_RATE_FMA_F32_F16> {
     }
     __device__ __forceinline__ static float out(V x) { return x; }
 };
-// Integer logic (lop3, three-input xor), the widening of BF16 taps
+template <> struct Step<IFDK_RATE_FMA_F32_BF16> {
+    using V = float;
+    static constexpr int LANES = 1;
+    __device__ __forceinline__ static V init(float s, int c) { return s + (float)c; }
+    __device__ __forceinline__ static void run(V &x, float b, float c)
+    {
+        const unsigned short hb = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+        const unsigned short hc = __bfloat16_as_ushort(__float2bfloat16_rn(c));
+        asm volatile("fma.rn.f32.bf16 %0, %1, %2, %0;" : "+f"(x) : "h"(hb), "h"(hc));
+    }
+    __device__ __forceinline__ static float out(V x) { return x; }
+};
+// Integer logic (lop3, three-input xor): the rate of the integer ops that widen
+// BF16 values (shift, mask) where a kernel widens them
 template <> struct Step<IFDK_RATE_LOP3> {
     using V = uint32_t;
     static constexpr int LANES = 1;
@@ -163,6 +177,10 @@ extern "C" int ifdk_arith_rate(int kind, int blocks, long long iters, float *sin
         rc = launch_rate<IFDK_RATE_FMA_F32_F16>(blocks, iters, sink, clocks, s);
         break;
     case IFDK_RATE_LOP3: lanes = 1; rc = launch_rate<IFDK_RATE_LOP3>(blocks, iters, sink, clocks, s); break;
+    case IFDK_RATE_FMA_F32_BF16:
+        lanes = 1;
+        rc = launch_rate<IFDK_RATE_FMA_F32_BF16>(blocks, iters, sink, clocks, s);
+        break;
     default: return IFDK_ERR_INVALID;
     }
     // instructions per thread, and lane operations per instruction

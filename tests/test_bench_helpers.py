@@ -48,12 +48,12 @@ def test_path_ceilings_from_rates():
     nominal 128-lane one; FP16 and BF16 paths get their instruction mixes."""
     r = {"ffma": {"lane_ops_per_clk_sm": 128.0}, "ffma2": {"lane_ops_per_clk_sm": 128.0},
          "hfma2": {"lane_ops_per_clk_sm": 256.0}, "fma_f32_f16": {"lane_ops_per_clk_sm": 128.0},
-         "lop3": {"lane_ops_per_clk_sm": 64.0}}
+         "lop3": {"lane_ops_per_clk_sm": 64.0}, "fma_f32_bf16": {"lane_ops_per_clk_sm": 128.0}}
     c = bench.path_ceilings(r, 152, 2.07e9)
     nominal = 152 * 128 * 2.07e9 / 10 / 2 ** 30
     assert abs(c["alu10"] - nominal) < 1e-9 * nominal and abs(c["f32"] - nominal) < 1e-9 * nominal
     assert abs(c["updates_per_clk_sm"]["f16"] - 1.0 / (3 / 128 + 6 / 256 + 1 / 128)) < 1e-12
-    assert abs(c["updates_per_clk_sm"]["bf16"] - 1.0 / (10 / 128 + 2 / 64)) < 1e-12
+    assert abs(c["updates_per_clk_sm"]["bf16"] - 1.0 / (8 / 128 + 2 / 128)) < 1e-12
     r["ffma2"]["lane_ops_per_clk_sm"] = 256.0           # a packed FMA that doubles the lane rate
     assert abs(bench.path_ceilings(r, 152, 2.07e9)["alu10"] - 2 * nominal) < 1e-9 * nominal
 

@@ -52,10 +52,11 @@ GEOMS = {
 TDT = {"float32": torch.float32, "float16": torch.float16, "bfloat16": torch.bfloat16}
 
 
-def pack_numpy(g, Q):
+def pack_numpy(g, Q, raw=False):
     """The packed layout written out: element (i, e) of detector row r = r0 + i
     and column c = e - 1 holds Q[r][c], Q[2vc-r][c], Q[r][c+1] - Q[r][c],
-    Q[2vc-r][c+1] - Q[2vc-r][c] (FP32 differences), Q zero off the detector."""
+    Q[2vc-r][c+1] - Q[2vc-r][c] (FP32 differences), Q zero off the detector;
+    raw (the BF16 layout): Q[r][c], Q[2vc-r][c], Q[r][c+1], Q[2vc-r][c+1]."""
     vc = (g.nv - 1) / 2 + g.off_v / g.dv
     two_vc = int(round(2 * vc))
     r0 = min(0, two_vc - (g.nv - 1))
@@ -70,8 +71,9 @@ def pack_numpy(g, Q):
     r = r0 + np.arange(rows)
     d, m = rowsof(r), rowsof(two_vc - r)
     a, b = d[..., :nu_p], m[..., :nu_p]
-    P = np.stack([a, b, d[..., 1:nu_p + 1] - a, m[..., 1:nu_p + 1] - b], -1)
-    return P
+    if raw:
+        return np.stack([a, b, d[..., 1:nu_p + 1], m[..., 1:nu_p + 1]], -1)
+    return np.stack([a, b, d[..., 1:nu_p + 1] - a, m[..., 1:nu_p + 1] - b], -1)
 
 
 @pytest.mark.parametrize("name", list(GEOMS))
@@ -82,7 +84,7 @@ def test_pack_is_the_packed_layout(name, dtype):
     gen = torch.Generator(device="cuda").manual_seed(7)
     Q = torch.randn((g.np, g.nv, g.nu), device="cuda", generator=gen).to(TDT[dtype])
     Qp = p.pack(Q)
-    ref = pack_numpy(g, Q.cpu().float().numpy())     # FP32 arithmetic on the stored values
+    ref = pack_numpy(g, Q.cpu().float().numpy(), raw=dtype == "bfloat16")   # FP32 arithmetic on the stored values
     ref = torch.from_numpy(ref).to(TDT[dtype]).float().numpy()   # rounded once to the storage type
     assert Qp.shape == ref.shape
     assert np.array_equal(Qp.cpu().float().numpy(), ref)
