@@ -585,6 +585,10 @@ def run_ours(args):
             main_bf.Q = main_bf.Qp = None      # the main arm's batch buffers are not needed any more
             storage_arms[key] = run_arm(plan, batches, dts[key], dev, args.standard, E, vol_main, acc,
                                         roofline_of, key)
+            if packed and storage_arms[key]["bp_path"] == "half-turn view pairs":
+                # DRAM bytes of one launch of this arm's kernel (committed ncu summary)
+                arm_rec = profile_record(kfile, f"bp_packed_{args.workload}_{key}")
+                storage_arms[key]["roofline"]["traffic"] = arm_rec.get("dram_bytes_per_launch")
         torch.cuda.synchronize()
         vol_for_acc = vol_main
     else:
