@@ -3,7 +3,9 @@
 Random detector and volume sizes (odd and even), pitches, source distances,
 offsets, start angles and view counts: the tensor-core filter, both
 back-projectors (packed with and without view pairing where the plan has
-them), FP16 storage (pairs and, where the scan allows, quads) and the adjoint, each against the FP64 oracle.  The same
+them), FP16 storage (pairs and, where the scan allows, quads), BF16 storage (against
+the oracle on the stored BF16 values) and the adjoint, each against the FP64
+oracle.  The same
 geometries pass the host emulation of the packed windows on the CPU."""
 import numpy as np
 import pytest
@@ -55,6 +57,14 @@ def test_random_geometry_parity(name):
             plan.set_view_pairing(mode)
             v16 = plan.backproject_packed(Qp16).cpu().double().numpy()
             assert rel_l2(v16, ref) <= 2e-3, mode
+        # BF16 packed views (raw taps, BF16 u weights) against the oracle on the stored values
+        Qb = plan.filter(Ed, dtype=torch.bfloat16)
+        ref_b = oracle.backproject(g, Qb.float().double().cpu().numpy())
+        Qpb = plan.pack(Qb)
+        for pairing in (True, False):
+            plan.set_view_pairing(pairing)
+            vb = plan.backproject_packed(Qpb).cpu().double().numpy()
+            assert rel_l2(vb, ref_b) <= 2e-3, pairing
     x = rng.standard_normal((g.nx, g.ny, g.nz)).astype(np.float32)
     P = plan.project(torch.from_numpy(x).cuda()).cpu().double().numpy()
     assert rel_l2(P, oracle.project(g, x.astype(np.float64))) <= 1e-5

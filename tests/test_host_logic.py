@@ -379,7 +379,7 @@ def test_packed_windows_random_geometries():
     geometries that the GPU parity sweep runs."""
     from tests.random_geometries import random_geometries
     for name, g in random_geometries():
-        for dt in (B.IFDK_F32, B.IFDK_F16):
+        for dt in (B.IFDK_F32, B.IFDK_F16, B.IFDK_BF16):
             for pairing in (True, False):
                 check_packed_windows(g, dt, pairing)
 
