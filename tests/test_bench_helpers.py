@@ -33,7 +33,7 @@ def test_clock_samples_median_max_and_reasons():
 def test_profile_record_matches_the_kernel_source():
     src = open(os.path.join(ROOT, "paper_1909_02724_gb300", "csrc", "ifdk_bp_packed.cu"), "rb").read()
     for name in ("bp_packed_fdk512_f32", "bp_packed_fdk512_f16", "bp_packed_fdk2048_f32", "bp_packed_fdk2048_f16",
-                 "bp_packed_fdk2048_bf16"):
+                 "bp_packed_fdk2048_bf16", "bp_packed_fdk2048_f16_quads"):
         rec = json.load(open(os.path.join(ROOT, "profiles", f"{name}.json")))
         got = bench.profile_record("ifdk_bp_packed.cu", name)
         if rec["source_sha1"] == hashlib.sha1(src).hexdigest():
