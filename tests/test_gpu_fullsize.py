@@ -110,9 +110,9 @@ def test_fdk2048_all_storage_types():
     run("fdk2048", ["f32", "f16", "bf16"], vox)
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f16"])
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 def test_fdk2048_in_batches_as_the_bench_runs_it(dtype):
-    """The benchmark's launch configuration: fdk2048 in 4 batches of 256 half-turn
+    """The benchmark's launch configuration (FP32, and the FP16 / BF16 arms): fdk2048 in 4 batches of 256 half-turn
     pairs (ifdk_filter_views, ifdk_pack_views, ifdk_backproject_packed_batch), against
     the FP64 oracle on sampled voxels of the top, middle and bottom slices."""
     from paper_1909_02724_gb300.api import BatchFdk
